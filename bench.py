@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Throughput of the fused pyramidal FAST + 3x3 NMS + cell-max detector.
+
+Default workload ("mixed64"): one step = one batched call over 64 frames
+(16 each of 640x480, 752x480, 1280x720, 1920x1080; seeds 2..65), 3 levels,
+FAST-9, threshold 15, 3x3 NMS, 32x32 cells, SAD-B score.  Inputs rotate over
+4 device-resident copies of the batch (4 x 58.6 MB > the 129 MB L2), so no
+step starts with its frames in L2.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & Mpixel/s detect+grid-NMS (batched/served vs plain), p50/p99 frame latency"
+
+WORKLOADS = {
+    "mixed64": dict(levels=3, thresh=15, arc=9, cell=32,
+                    desc="64 frames in one batched launch: 16 each of 640x480, 752x480, 1280x720, "
+                         "1920x1080 (seeds 2..65, 40 shapes), 3-level pyramid, FAST-9, thresh 15, "
+                         "3x3 NMS, 32x32 cells, SAD-B"),
+    "single752": dict(levels=3, thresh=20, arc=9, cell=32,
+                      desc="one 752x480 frame (seed 1), 3-level pyramid, FAST-9, thresh 20, 3x3 NMS, "
+                           "32x32 cells, SAD-B"),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mixed64")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline leg")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/profile legs")
+    ap.add_argument("--spin", type=float, default=0.5, help="seconds of untimed steps before timing")
+    return ap.parse_args()
+
+
+def make_frames(workload: str):
+    from paper_2003_13493_gb300 import synth
+
+    if workload == "mixed64":
+        return synth.mixed_batch(first_seed=2, per_size=16)
+    return [synth.make_frame(752, 480, seed=1)]
+
+
+# ---- clocks -------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu=timestamp,{self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def mark(self, which: str):
+        setattr(self, which, time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for r in csv.reader(io.StringIO(out)):
+            if len(r) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(r[0].strip().split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, [c.strip() for c in r[1:]]))
+            except ValueError:
+                continue
+        inside = [v for ts, v in rows if self.t0 is not None and self.t0 - 1 <= ts <= self.t1 + 1]
+        use = inside or [v for _, v in rows]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(v[1]) for v in use if v[1].replace(".", "").isdigit()]
+        mx = [float(v[2]) for v in use if v[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for v in use:
+            for name, val in zip(names, v[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(use), "samples_in_window": len(inside)}
+
+
+# ---- ncu traffic recorded for the current kernel source ------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_2003_13493_gb300/csrc/vio_kernels.cuh", "paper_2003_13493_gb300/csrc/ptx.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """dram bytes per launch of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"fast_nms_cell_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    src = traffic = None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("kernel_source_sha256:"):
+                src = line.split(":", 1)[1].strip()
+            if line.startswith("dram_bytes_per_launch:"):
+                traffic = float(line.split(":", 1)[1].strip())
+    return traffic if src == kernel_source_hash() else None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ---- CPU oracle leg ------------------------------------------------------------
+
+def oracle_rate(frames, wl, seconds: float):
+    """Frames/s of the plain C oracle over a bounded sample, frame-parallel on
+    the host cores (ctypes releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    oracle.build()
+    by_size = {}
+    for f in frames:
+        by_size.setdefault(f.shape, []).append(f)
+    sample = [v[i] for v in by_size.values() for i in range(min(2, len(v)))]
+    cores = os.cpu_count() or 1
+    done = 0
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        while True:
+            list(ex.map(lambda im: oracle.detect(im, wl["thresh"], wl["arc"], wl["cell"], wl["levels"]),
+                        sample))
+            done += len(sample)
+            if time.perf_counter() - t0 >= seconds:
+                break
+    dt = time.perf_counter() - t0
+    desc = "+".join(f"{len(v[:2])}x{s[1]}x{s[0]}" for s, v in by_size.items())
+    return done / dt, cores, f"{desc} frames of the workload, repeated {done // len(sample)}x ({dt:.1f} s)"
+
+
+# ---- our implementation ------------------------------------------------------------
+
+def algorithmic_bytes(dims, levels, cell, num_cells):
+    """Per-step bytes and the fused kernel's bytes per launch."""
+    step = 0.0
+    fused = 0.0
+    for (w, h) in dims:
+        nc = num_cells(w, h, cell)
+        pyr_px = sum((w >> k) * (h >> k) for k in range(1, levels))
+        all_px = sum((w >> k) * (h >> k) for k in range(levels))
+        step += w * h + 2 * pyr_px + 16 * nc
+        fused += all_px + 8 * nc
+    return step, fused
+
+
+def run_ours(args, rank, world, local_rank):
+    import ctypes
+
+    import torch
+
+    from paper_2003_13493_gb300 import vio
+
+    wl = WORKLOADS[args.workload]
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    frames_np = make_frames(args.workload)
+    n = len(frames_np)
+    dims = [(f.shape[1], f.shape[0]) for f in frames_np]
+    mpx = sum(w * h for w, h in dims) / 1e6
+    sets = 4 if args.workload == "mixed64" else 64
+    stream = torch.cuda.Stream(device=dev)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+
+    det = vio.Detector(device=local_rank, max_frames=max(64, n), autotune=True)
+    dev_sets = []
+    with torch.cuda.stream(stream):
+        for _ in range(sets):
+            dev_sets.append([torch.from_numpy(f).to(dev) for f in frames_np])
+    outs = [torch.empty((vio.num_cells(w, h, wl["cell"]), 4), dtype=torch.int32, device=dev) for w, h in dims]
+    counts = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def marshal(frames):
+        d = (vio.Dims * n)(*[vio.Dims(f.shape[1], f.shape[0], f.stride(0)) for f in frames])
+        fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in frames])
+        return fp, d
+
+    marshalled = [marshal(s) for s in dev_sets]
+    optr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    cptr = ctypes.c_void_p(counts.data_ptr())
+
+    def step(i, d=det):
+        fp, dd = marshalled[i % sets]
+        d.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], optr, cptr, sh)
+
+    for i in range(max(3, args.warmup)):
+        step(i)
+    det.sync(stream)
+    tune = det.tuning()
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    # bring clocks up before the timed region
+    t_spin = time.perf_counter()
+    i = 0
+    while time.perf_counter() - t_spin < args.spin:
+        step(i)
+        i += 1
+    det.sync(stream)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks.mark("t0")
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    e1.record(stream)
+    det.sync(stream)
+    torch.cuda.synchronize(dev)
+    clocks.mark("t1")
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    fps = world * n * args.steps / (ms / 1e3)
+
+    res = {
+        "metric": METRIC, "value": round(fps, 1), "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded value noise + shapes, integer generator)",
+        "mpixel_per_s": round(world * mpx * args.steps / (ms / 1e3), 1),
+        "config": {"workload": f"{args.workload}: {wl['desc']}", "frames_per_step": n,
+                   "mpixel_per_step": round(mpx, 3), "levels": wl["levels"], "thresh": wl["thresh"],
+                   "arc_len": wl["arc"], "cell": wl["cell"], "score": "SAD-B",
+                   "l2": f"inputs rotate over {sets} device copies of the batch "
+                         f"({sets * mpx:.0f} MB > 129 MB L2)",
+                   "tile": {"w": tune[0], "h": tune[1], "variant": tune[2], "picked_by": "autotuner"},
+                   "parallelism": f"replicas x{world}, no collective"},
+        "clocks": clk,
+        "gpu_launches": args.steps * (3 if wl["levels"] > 1 else 2),
+    }
+    if rank == 0 and not args.no_extras:
+        res.update(extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cptr, n, mpx,
+                          ms_per_step))
+    det.close()
+    return res
+
+
+def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cptr, n, mpx, ms_per_step):
+    import ctypes
+
+    import torch
+
+    from paper_2003_13493_gb300 import vio
+
+    out = {}
+    # roofline of the fused kernel: stage events captured inside the graph
+    prof = vio.Detector(device=dev.index, max_frames=max(64, n), profile=True)
+    prof.set_variant(det.tuning()[2])
+    steps = min(args.steps, 200)
+    acc = [0.0, 0.0, 0.0]
+    for i in range(steps + 3):
+        fp, dd = marshalled[i % len(marshalled)]
+        prof.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], optr, cptr, sh)
+        st = prof.stage_ms()
+        if i >= 3:
+            acc = [a + b for a, b in zip(acc, st)]
+    prof.close()
+    stage = [a / steps for a in acc]
+    step_bytes, fused_bytes = algorithmic_bytes(dims, wl["levels"], wl["cell"], vio.num_cells)
+    peaks, kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = fused_bytes / (stage[1] * 1e-3) / 1e9
+    traffic = recorded_traffic(args.workload)
+    out["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                       "frac": round(achieved / peak, 4), "traffic": traffic,
+                       "kernel": "fast_nms_cell_kernel", "peak_kind": f"{kind} hbm_gbs",
+                       "algorithmic_bytes_per_launch": int(fused_bytes)}
+    out["stage_ms"] = {"pyramid": round(stage[0], 5), "fast_nms_cell": round(stage[1], 5),
+                       "decode": round(stage[2], 5)}
+    step_gbs = step_bytes / (ms_per_step * 1e-3) / 1e9
+    out["step_roofline"] = {"algorithmic_bytes_per_step": int(step_bytes), "achieved_gbs": round(step_gbs, 1),
+                            "frac": round(step_gbs / peak, 4),
+                            "what": "whole step (pyramid + fused detect + decode) against the HBM peak"}
+
+    # plain path: one frame per call
+    plain = vio.Detector(device=dev.index, max_frames=4)
+    plain.set_variant(det.tuning()[2])
+    single = [((ctypes.c_void_p * 1)(marshalled[s][0][i]), (vio.Dims * 1)(marshalled[s][1][i]),
+               (ctypes.c_void_p * 1)(optr[i])) for s in range(len(marshalled)) for i in range(n)]
+    psteps = max(3, min(args.steps, 100))
+    for j in range(n * 2):
+        fp, dd, op = single[j % len(single)]
+        plain.detect_ptrs(fp, dd, 1, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], op, None, sh)
+    plain.sync(stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for j in range(psteps * n):
+        fp, dd, op = single[j % len(single)]
+        plain.detect_ptrs(fp, dd, 1, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], op, None, sh)
+    e1.record(stream)
+    plain.sync(stream)
+    pms = e0.elapsed_time(e1)
+    plain.close()
+    out["plain"] = {"value": round(psteps * n / (pms / 1e3), 1), "unit": "frames/s",
+                    "what": "same frames, one vio_detect call (and graph replay) per frame"}
+
+    # end to end through the host-buffer entry point (pinned host frames)
+    pinned = [torch.from_numpy(f).pin_memory() for f in frames_np]
+    host_frames = [p.numpy() for p in pinned]
+    host_outs = [torch.empty((vio.num_cells(w, h, wl["cell"]), 4), dtype=torch.int32).pin_memory().numpy()
+                 for w, h in dims]
+    host_counts = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    e2e_det = vio.Detector(device=dev.index, max_frames=max(64, n))
+    e2e_det.set_variant(det.tuning()[2])
+    for _ in range(3):
+        e2e_det.detect_host(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], host_outs,
+                            host_counts, stream)
+    esteps = max(3, min(args.steps, 50))
+    t0 = time.perf_counter()
+    for _ in range(esteps):
+        e2e_det.detect_host(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], host_outs,
+                            host_counts, stream)
+    dt = time.perf_counter() - t0
+    e2e_det.close()
+    h2d = sum(w * h for w, h in dims)
+    d2h = sum(16 * vio.num_cells(w, h, wl["cell"]) for w, h in dims) + 4 * n
+    out["e2e"] = {"value": round(esteps * n / dt, 1), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": d2h, "steps": esteps,
+                  "what": "vio_detect_host: pinned host frames -> device -> detect -> host cells, synchronous"}
+
+    if not args.no_cpu_baseline:
+        rate, cores, sample = oracle_rate(frames_np, wl, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": round(rate, 2), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                               "sample": sample}
+    return out
+
+
+def run_reference(args, rank, world):
+    wl = WORKLOADS[args.workload]
+    frames = make_frames(args.workload)
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for _ in range(max(0, args.warmup)):
+        oracle_rate(frames, wl, 0.0)
+    total = 0.0
+    t0 = time.perf_counter()
+    rates = []
+    cores = sample = None
+    for _ in range(args.steps):
+        r, cores, sample = oracle_rate(frames, wl, per_step)
+        rates.append(r)
+    dt = time.perf_counter() - t0
+    total = sum(rates) / len(rates)
+    return {"metric": METRIC, "value": round(total, 2), "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded value noise + shapes, integer generator)", "impl": "reference",
+            "config": {"workload": f"{args.workload}: {wl['desc']}"},
+            "cpu_baseline": {"value": round(total, 2), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(total, 2), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

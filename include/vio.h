@@ -1,0 +1,192 @@
+/*
+ * vio.h -- C ABI of the GB300 (sm_103a) pyramidal FAST detector with fused
+ * 3x3 non-maxima suppression and one-feature-per-cell selection.
+ *
+ * What is computed (Nagy, Foehn, Scaramuzza, "Faster than FAST:
+ * GPU-Accelerated Frontend for High-Speed VIO", IROS 2020):
+ *
+ *   Algorithm 1 (Section II-B): for every pyramid level, every pixel is put
+ *   through the FAST segment test and scored (CRF); non-maxima suppression
+ *   runs per level (NMS); then one feature per grid cell is kept over all
+ *   levels (NMS-C).
+ *
+ *   Pyramid (Section II-B, Section III-C "each subsequent layer halves the
+ *   resolution"): level k+1 is (W_k >> 1) x (H_k >> 1), each pixel the 2x2
+ *   mean of level k rounded half up: (a + b + c + d + 2) >> 2.
+ *
+ *   Segment test (Section II-D, Eq. 1): the 16 points of the radius-3
+ *   Bresenham circle are darker (I_x < I_c - thresh), brighter
+ *   (I_x > I_c + thresh) or similar; the pixel is a corner when a
+ *   contiguous arc of at least arc_len points is all darker or all
+ *   brighter.  Pixels closer than 3 to a level border are not tested.
+ *
+ *   Scores (Section II-D): SAD-B = sum |I_x - I_c| over the circle;
+ *   SAD-A = the same sum over the contiguous arc; MT = the largest
+ *   threshold at which the pixel is still a corner; 0 if not a corner.
+ *
+ *   NMS (Algorithm 1, n = 1 of Section I-B): a pixel survives when its score
+ *   is > 0 and >= the scores of its 8 neighbours (outside the level: 0).
+ *
+ *   NMS-C (Section II-B grid cells, Section II-C single grid over all
+ *   levels): the level-0 image is cut into ceil(W/C) x ceil(H/C) cells of
+ *   C x C pixels; a survivor (x, y) of level k belongs to cell
+ *   ((x << k) / C, (y << k) / C).  Each cell reports its best survivor:
+ *   highest score, then lower level, then lower y, then lower x.  The
+ *   record is {x << k, y << k, k, score}; an empty cell is {-1, -1, -1, 0}.
+ *   The result is unique, so the library's output is bit-exact.
+ *
+ * Conventions
+ *   - Every call returns a vio_status; nothing aborts or prints.  Argument
+ *     checks run on the host before anything is enqueued.
+ *   - Device calls are asynchronous on the given stream (a cudaStream_t
+ *     passed as vio_stream; NULL = the legacy default stream).  A CUDA error
+ *     met while enqueuing returns VIO_ERR_CUDA; a device-side wait that ran
+ *     out of time is reported by vio_sync() as VIO_ERR_TIMEOUT.
+ *   - Ownership: caller-owned buffers stay caller-owned and are only read
+ *     (frames) or written (outputs) by work enqueued on the stream.  The
+ *     context owns its resident pyramid, cell-key, descriptor and
+ *     tensor-map buffers; they grow on demand up to mem_budget_bytes
+ *     (VIO_ERR_OOM past it).
+ *   - Threading: a context serves one host thread at a time.
+ */
+#ifndef VIO_H_
+#define VIO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VIO_ABI_VERSION 1
+#define VIO_MAX_LEVELS 5
+
+typedef struct vio_ctx vio_ctx;
+/* A cudaStream_t, declared without pulling in the CUDA headers. */
+typedef struct CUstream_st* vio_stream;
+
+typedef enum {
+    VIO_OK = 0,
+    VIO_ERR_INVALID_ARG = 1, /* an argument is outside its documented range */
+    VIO_ERR_OOM = 2,         /* device memory or the context budget ran out */
+    VIO_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed            */
+    VIO_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up           */
+    VIO_ERR_BUSY = 5,        /* serving queue full                           */
+    VIO_ERR_UNSUPPORTED = 6, /* the device is not an sm_103 GPU              */
+    VIO_ERR_NOT_FOUND = 7    /* unknown serving ticket                       */
+} vio_status;
+
+typedef enum { VIO_SCORE_SAD_B = 0, VIO_SCORE_SAD_A = 1, VIO_SCORE_MT = 2 } vio_score;
+
+typedef struct {
+    int device;              /* CUDA device ordinal                                  */
+    size_t mem_budget_bytes; /* 0 = no limit beyond device memory                    */
+    int max_frames;          /* most frames one vio_detect call may carry (1..1024)  */
+    int score;               /* a vio_score                                          */
+    int autotune;            /* 1 = time tile shapes on the first call of a shape    */
+    int use_graphs;          /* 1 = replay each batch shape as a captured CUDA graph */
+    int profile;             /* 1 = record CUDA events around each stage (vio_stage_ms) */
+} vio_config;
+
+/* One frame: width, height, row pitch in bytes (pitch >= w). */
+typedef struct {
+    int32_t w, h, pitch;
+} vio_dims;
+
+/* One cell of the output grid (16 bytes); empty cell = {-1, -1, -1, 0}. */
+typedef struct {
+    int32_t x, y, level, score;
+} vio_feature;
+
+/* Fills *cfg with the defaults: device 0, no budget, 64 frames, SAD-B,
+ * autotune off, graphs on, profiling off. */
+void vio_config_default(vio_config* cfg);
+
+/* Creates a context on cfg->device.  *out receives the context or NULL.
+ * Errors: VIO_ERR_INVALID_ARG (NULL pointers, ranges), VIO_ERR_UNSUPPORTED
+ * (device is not compute capability 10.3), VIO_ERR_CUDA, VIO_ERR_OOM. */
+vio_status vio_create(vio_ctx** out, const vio_config* cfg);
+
+/* Waits for the context's work, frees all of its buffers.  NULL is a no-op. */
+vio_status vio_destroy(vio_ctx* ctx);
+
+/* Static English description of a status. */
+const char* vio_status_str(vio_status s);
+
+/* The last error message recorded by the context (static storage of the
+ * context, valid until its next call). */
+const char* vio_last_error(const vio_ctx* ctx);
+
+/* Number of cells ceil(w/cell) * ceil(h/cell); 0 when an argument is < 1. */
+size_t vio_num_cells(int w, int h, int cell_size);
+
+/*
+ * Detects features in n_frames frames with one batched launch.
+ *
+ *   frames     host array of n_frames DEVICE pointers to uint8 frames.  A
+ *              frame whose address is not 16-byte aligned or whose pitch is
+ *              not a multiple of 16 is first copied into a context slot.
+ *   dims       host array of n_frames vio_dims.
+ *   thresh     0..255 (>= 1 when the context scores with MT, whose score
+ *              would otherwise be 0 for a corner).
+ *   arc_len    9..16.
+ *   cell_size  a positive multiple of 32 (Section II-C: cell widths are
+ *              multiples of the 32-thread warp).
+ *   levels     1..VIO_MAX_LEVELS; the smallest level must be >= 7 x 7.
+ *   out_cells  host array of n_frames DEVICE pointers, frame i receiving
+ *              vio_num_cells(w_i, h_i, cell_size) vio_feature records in
+ *              row-major cell order.
+ *   out_counts DEVICE int32[n_frames] receiving the number of non-empty
+ *              cells per frame, or NULL.
+ *
+ * Each frame must satisfy 7 <= w, 7 <= h and w * h < 2^28.  Asynchronous
+ * on `stream`.  Errors: VIO_ERR_INVALID_ARG, VIO_ERR_OOM, VIO_ERR_CUDA.
+ */
+vio_status vio_detect(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims* dims, int n_frames,
+                      int thresh, int arc_len, int cell_size, int levels,
+                      vio_feature* const* out_cells, int32_t* out_counts, vio_stream stream);
+
+/*
+ * Same as vio_detect for frames and results in HOST memory: the frames are
+ * copied into resident device slots, detected, and the cells copied back;
+ * the call returns when out_cells (host, per frame) and out_counts (host
+ * int32[n_frames] or NULL) are written.  Pinned host memory makes the
+ * copies asynchronous; pageable memory works too.
+ */
+vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims,
+                           int n_frames, int thresh, int arc_len, int cell_size, int levels,
+                           vio_feature* const* host_cells, int32_t* host_counts, vio_stream stream);
+
+/* Stage durations of the context's most recent vio_detect call, in ms:
+ * ms[0] pyramid, ms[1] fused FAST + NMS + cell max, ms[2] decode.  Needs
+ * profile = 1 in the config; waits for that call to finish.  The events are
+ * recorded on the call's stream (inside the replayed graph when graphs are
+ * on), so the figures are device time of each kernel. */
+vio_status vio_stage_ms(vio_ctx* ctx, float* ms3);
+
+/* Waits for all work the context enqueued on `stream` and reports any
+ * device-side status (VIO_ERR_TIMEOUT when a bounded wait gave up). */
+vio_status vio_sync(vio_ctx* ctx, vio_stream stream);
+
+/*
+ * Tile configuration of the fused kernel.  tile_w x tile_h level pixels per
+ * work item, cta_per_sm resident CTAs per SM for the persistent launch.
+ * vio_get_tuning reports the configuration in use; vio_set_tuning pins one
+ * (VIO_ERR_INVALID_ARG if it is not one of the built variants).
+ */
+typedef struct {
+    int tile_w, tile_h, cta_per_sm, variant;
+} vio_tuning;
+
+vio_status vio_get_tuning(const vio_ctx* ctx, vio_tuning* out);
+vio_status vio_set_tuning(vio_ctx* ctx, const vio_tuning* t);
+/* Number of built variants and the shape of variant i. */
+int vio_num_variants(void);
+vio_status vio_variant(int i, vio_tuning* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIO_H_ */

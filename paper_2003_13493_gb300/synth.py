@@ -123,7 +123,7 @@ def make_frame(w: int, h: int, seed: int, n_shapes: int = 40) -> np.ndarray:
     lat, used = _lattice(w, h, seed)
     img = _texture(w, h, lat)
     _paint_shapes(img, seed, n_shapes, used)
-    return np.clip(img, 0, 255).astype(np.uint8)
+    return np.ascontiguousarray(np.clip(img, 0, 255).astype(np.uint8))
 
 
 def frame_sha256(img: np.ndarray) -> str:

@@ -1,0 +1,237 @@
+"""Thin ctypes binding of ``include/vio.h``.
+
+Argument marshalling only: every step of the detector runs in the CUDA
+library.  PyTorch provides device memory (``tensor.data_ptr()``) and streams
+(``torch.cuda.Stream.cuda_stream``).  Loading fails loudly when the library
+has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+SCORE_SAD_B, SCORE_SAD_A, SCORE_MT = 0, 1, 2
+MAX_LEVELS = 5
+
+STATUS = {0: "VIO_OK", 1: "VIO_ERR_INVALID_ARG", 2: "VIO_ERR_OOM", 3: "VIO_ERR_CUDA",
+          4: "VIO_ERR_TIMEOUT", 5: "VIO_ERR_BUSY", 6: "VIO_ERR_UNSUPPORTED", 7: "VIO_ERR_NOT_FOUND"}
+
+
+class VioError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
+                ("max_frames", ctypes.c_int), ("score", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("use_graphs", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("pitch", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
+                ("cta_per_sm", ctypes.c_int), ("variant", ctypes.c_int)]
+
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/vio.h."""
+    with open(os.path.join(_build.INCLUDE, "vio.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vio_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Loads the library (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path}")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    ci = ctypes.c_int
+    st = ctypes.c_int
+    lib.vio_config_default.argtypes = [ctypes.POINTER(Config)]
+    lib.vio_config_default.restype = None
+    lib.vio_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Config)]
+    lib.vio_create.restype = st
+    lib.vio_destroy.argtypes = [P]
+    lib.vio_destroy.restype = st
+    lib.vio_status_str.argtypes = [st]
+    lib.vio_status_str.restype = ctypes.c_char_p
+    lib.vio_last_error.argtypes = [P]
+    lib.vio_last_error.restype = ctypes.c_char_p
+    lib.vio_num_cells.argtypes = [ci, ci, ci]
+    lib.vio_num_cells.restype = ctypes.c_size_t
+    detect_args = [P, ctypes.POINTER(P), ctypes.POINTER(Dims), ci, ci, ci, ci, ci, ctypes.POINTER(P), P, P]
+    lib.vio_detect.argtypes = detect_args
+    lib.vio_detect.restype = st
+    lib.vio_detect_host.argtypes = detect_args
+    lib.vio_detect_host.restype = st
+    lib.vio_sync.argtypes = [P, P]
+    lib.vio_sync.restype = st
+    lib.vio_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    lib.vio_stage_ms.restype = st
+    lib.vio_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+    lib.vio_get_tuning.restype = st
+    lib.vio_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+    lib.vio_set_tuning.restype = st
+    lib.vio_num_variants.argtypes = []
+    lib.vio_num_variants.restype = ci
+    lib.vio_variant.argtypes = [ci, ctypes.POINTER(Tuning)]
+    lib.vio_variant.restype = st
+    _lib = lib
+    return lib
+
+
+def num_cells(w: int, h: int, cell: int) -> int:
+    return int(load().vio_num_cells(w, h, cell))
+
+
+def variants() -> list[tuple[int, int]]:
+    lib = load()
+    out = []
+    for i in range(lib.vio_num_variants()):
+        t = Tuning()
+        lib.vio_variant(i, ctypes.byref(t))
+        out.append((t.tile_w, t.tile_h))
+    return out
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    h = getattr(stream, "cuda_stream", stream)
+    return ctypes.c_void_p(int(h) if h else 0)
+
+
+class Detector:
+    """One library context on one device."""
+
+    def __init__(self, device: int = 0, max_frames: int = 64, score: int = SCORE_SAD_B,
+                 mem_budget_bytes: int = 0, autotune: bool = False, use_graphs: bool = True,
+                 profile: bool = False):
+        self.lib = load()
+        cfg = Config()
+        self.lib.vio_config_default(ctypes.byref(cfg))
+        cfg.device = device
+        cfg.max_frames = max_frames
+        cfg.score = score
+        cfg.mem_budget_bytes = mem_budget_bytes
+        cfg.autotune = int(autotune)
+        cfg.use_graphs = int(use_graphs)
+        cfg.profile = int(profile)
+        self.cfg = cfg
+        self.ctx = ctypes.c_void_p()
+        s = self.lib.vio_create(ctypes.byref(self.ctx), ctypes.byref(cfg))
+        if s != 0:
+            raise VioError(s, self.lib.vio_status_str(s).decode())
+
+    def close(self):
+        if self.ctx:
+            self.lib.vio_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s: int):
+        if s != 0:
+            raise VioError(s, self.lib.vio_last_error(self.ctx).decode())
+
+    def detect(self, frames, thresh: int, arc_len: int, cell: int, levels: int,
+               outs=None, counts=None, stream=None):
+        """frames: list of 2-D uint8 CUDA tensors (row stride = pitch).
+        Returns (list of (ncells, 4) int32 CUDA tensors, int32 counts tensor)."""
+        import torch
+
+        n = len(frames)
+        dims = (Dims * n)()
+        fptr = (ctypes.c_void_p * n)()
+        for i, f in enumerate(frames):
+            if f.dtype != torch.uint8 or f.dim() != 2 or f.stride(1) != 1 or not f.is_cuda:
+                raise ValueError("frames must be 2-D uint8 CUDA tensors with unit column stride")
+            dims[i] = Dims(f.shape[1], f.shape[0], f.stride(0))
+            fptr[i] = f.data_ptr()
+        dev = frames[0].device
+        if outs is None:
+            outs = [torch.empty((num_cells(d.w, d.h, cell), 4), dtype=torch.int32, device=dev) for d in dims]
+        if counts is None:
+            counts = torch.empty(n, dtype=torch.int32, device=dev)
+        optr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        self._check(self.lib.vio_detect(self.ctx, fptr, dims, n, thresh, arc_len, cell, levels, optr,
+                                        ctypes.c_void_p(counts.data_ptr()), _stream_handle(stream)))
+        return outs, counts
+
+    def detect_ptrs(self, fptr, dims, n, thresh, arc_len, cell, levels, optr, counts_ptr, stream_handle):
+        """Pre-marshalled call (ctypes arrays), for timing loops."""
+        self._check(self.lib.vio_detect(self.ctx, fptr, dims, n, thresh, arc_len, cell, levels, optr,
+                                        counts_ptr, stream_handle))
+
+    def detect_host(self, frames, thresh: int, arc_len: int, cell: int, levels: int,
+                    outs=None, counts=None, stream=None):
+        """frames: list of 2-D uint8 numpy arrays (host).  Returns numpy results."""
+        n = len(frames)
+        dims = (Dims * n)()
+        fptr = (ctypes.c_void_p * n)()
+        for i, f in enumerate(frames):
+            if f.dtype != np.uint8 or f.ndim != 2 or f.strides[1] != 1:
+                raise ValueError("frames must be 2-D uint8 arrays with unit column stride")
+            dims[i] = Dims(f.shape[1], f.shape[0], f.strides[0])
+            fptr[i] = f.ctypes.data
+        if outs is None:
+            outs = [np.empty((num_cells(d.w, d.h, cell), 4), dtype=np.int32) for d in dims]
+        if counts is None:
+            counts = np.empty(n, dtype=np.int32)
+        optr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+        self._check(self.lib.vio_detect_host(self.ctx, fptr, dims, n, thresh, arc_len, cell, levels, optr,
+                                             ctypes.c_void_p(counts.ctypes.data),
+                                             _stream_handle(stream) if stream is not None else ctypes.c_void_p(0)))
+        return outs, counts
+
+    def stage_ms(self) -> tuple[float, float, float]:
+        """(pyramid, fused detect, decode) device ms of the last call."""
+        ms = (ctypes.c_float * 3)()
+        self._check(self.lib.vio_stage_ms(self.ctx, ms))
+        return ms[0], ms[1], ms[2]
+
+    def sync(self, stream=None):
+        self._check(self.lib.vio_sync(self.ctx, _stream_handle(stream)))
+
+    def set_variant(self, variant: int | None):
+        if variant is None:
+            self._check(self.lib.vio_set_tuning(self.ctx, None))
+            return
+        t = Tuning(0, 0, 0, variant)
+        self._check(self.lib.vio_set_tuning(self.ctx, ctypes.byref(t)))
+
+    def tuning(self) -> tuple[int, int, int]:
+        t = Tuning()
+        self._check(self.lib.vio_get_tuning(self.ctx, ctypes.byref(t)))
+        return t.tile_w, t.tile_h, t.variant

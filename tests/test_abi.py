@@ -1,0 +1,65 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+function include/vio.h declares; pure host helpers behave; without a GPU the
+context constructor fails with a status instead of crashing."""
+import ctypes
+
+import pytest
+
+from paper_2003_13493_gb300 import vio
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return vio.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = vio.header_functions()
+    assert "vio_detect" in names and "vio_create" in names and "vio_destroy" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_num_cells(lib):
+    assert vio.num_cells(752, 480, 32) == 24 * 15
+    assert vio.num_cells(1920, 1080, 32) == 60 * 34
+    assert vio.num_cells(3840, 2160, 64) == 60 * 34
+    assert vio.num_cells(32, 32, 32) == 1
+    assert vio.num_cells(33, 32, 32) == 2
+    assert vio.num_cells(0, 10, 32) == 0
+    assert vio.num_cells(10, 10, 0) == 0
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.vio_status_str(s)
+    assert lib.vio_status_str(99) == b"unknown status"
+
+
+def test_config_default(lib):
+    cfg = vio.Config()
+    lib.vio_config_default(ctypes.byref(cfg))
+    assert (cfg.device, cfg.max_frames, cfg.score, cfg.autotune, cfg.use_graphs) == (0, 64, 0, 0, 1)
+
+
+def test_variants_listed(lib):
+    vs = vio.variants()
+    assert len(vs) >= 3
+    for tw, th in vs:
+        assert tw % 16 == 0 and tw + 32 <= 256 and th + 8 <= 256
+    t = vio.Tuning()
+    assert lib.vio_variant(len(vs), ctypes.byref(t)) == 1
+
+
+def test_create_rejects_bad_config_and_null(lib):
+    assert lib.vio_create(None, None) == 1
+    cfg = vio.Config()
+    lib.vio_config_default(ctypes.byref(cfg))
+    cfg.max_frames = 0
+    ctx = ctypes.c_void_p()
+    assert lib.vio_create(ctypes.byref(ctx), ctypes.byref(cfg)) == 1
+    assert not ctx
+
+
+def test_destroy_null_is_noop(lib):
+    assert lib.vio_destroy(None) == 0

@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the CPU
+oracle, element by element, bit-exact (integer arithmetic throughout)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_13493_gb300 import synth, vio
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dets():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    out = {m: vio.Detector(device=0, max_frames=64, score=m) for m in (0, 1, 2)}
+    yield out
+    for d in out.values():
+        d.close()
+
+
+def to_gpu(img, pitch=None, offset=0):
+    """Device copy of img with row pitch `pitch` and base offset `offset` bytes."""
+    h, w = img.shape
+    pitch = pitch or w
+    buf = torch.zeros(h * pitch + offset + 64, dtype=torch.uint8, device="cuda")
+    view = buf[offset:offset + h * pitch].view(h, pitch)[:, :w]
+    view.copy_(torch.from_numpy(img).cuda())
+    return view
+
+
+def run(det, imgs, thresh, arc, cell, levels, **kw):
+    frames = [to_gpu(im, **kw) for im in imgs]
+    outs, counts = det.detect(frames, thresh, arc, cell, levels)
+    det.sync()
+    return [o.cpu().numpy() for o in outs], counts.cpu().numpy()
+
+
+def assert_parity(got, counts, imgs, thresh, arc, cell, levels, mode):
+    for i, img in enumerate(imgs):
+        want, n = oracle.detect(img, thresh, arc, cell, levels, mode)
+        if not np.array_equal(got[i], want):
+            bad = np.nonzero((got[i] != want).any(axis=1))[0]
+            raise AssertionError(f"frame {i} ({img.shape[1]}x{img.shape[0]}): {len(bad)} cells differ, "
+                                 f"first {bad[:3].tolist()}: got {got[i][bad[:3]].tolist()} "
+                                 f"want {want[bad[:3]].tolist()}")
+        assert counts[i] == n, (i, counts[i], n)
+
+
+# ---- the five workloads ----------------------------------------------------
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_single_frame_one_level(dets, mode):
+    img = synth.make_frame(752, 480, seed=0)
+    got, cnt = run(dets[mode], [img], 10, 9, 32, 1)
+    assert_parity(got, cnt, [img], 10, 9, 32, 1, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_single_frame_three_levels(dets, mode):
+    img = synth.make_frame(752, 480, seed=1)
+    got, cnt = run(dets[mode], [img], 20, 9, 32, 3)
+    assert_parity(got, cnt, [img], 20, 9, 32, 3, mode)
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    return synth.mixed_batch(first_seed=2, per_size=16)
+
+
+@pytest.mark.parametrize("cell", [32, 64])
+def test_mixed_batch_64_frames(dets, mixed, cell):
+    got, cnt = run(dets[0], mixed, 15, 9, cell, 3)
+    assert_parity(got, cnt, mixed, 15, 9, cell, 3, 0)
+
+
+def test_large_frames_sampled(dets):
+    """3840x2160, 4 levels, 64x64 cells: two frames of the 32-frame set in
+    one launch, all eight (arc, thresh) combinations checked on frame 0 and
+    one combination on frame 1."""
+    imgs = [synth.make_frame(3840, 2160, seed=100 + i, n_shapes=400) for i in range(2)]
+    frames = [to_gpu(im) for im in imgs]
+    for arc in (12, 9):
+        for thresh in (5, 10, 20, 40):
+            outs, counts = dets[0].detect(frames, thresh, arc, 64, 4)
+            dets[0].sync()
+            got = [o.cpu().numpy() for o in outs]
+            cnt = counts.cpu().numpy()
+            check = imgs if (arc, thresh) == (9, 10) else imgs[:1]
+            assert_parity(got, cnt, check, thresh, arc, 64, 4, 0)
+
+
+# ---- edge cases -------------------------------------------------------------
+
+EDGE_SIZES = [(7, 7, 1), (8, 7, 1), (13, 9, 1), (31, 17, 1), (100, 37, 2), (257, 131, 3),
+              (640, 480, 4), (1920, 1080, 5), (333, 999, 3), (4000, 70, 3), (56, 56, 3)]
+
+
+@pytest.mark.parametrize("w,h,levels", EDGE_SIZES)
+def test_ragged_sizes(dets, w, h, levels):
+    img = synth.make_frame(w, h, seed=w * 1000 + h, n_shapes=10)
+    for mode in (0, 1, 2):
+        got, cnt = run(dets[mode], [img], 8, 9, 32, levels)
+        assert_parity(got, cnt, [img], 8, 9, 32, levels, mode)
+
+
+def test_pitch_and_alignment_paths(dets):
+    img = synth.make_frame(301, 203, seed=4, n_shapes=12)
+    for pitch, offset in ((None, 0), (304, 0), (320, 0), (301, 1), (512, 16), (320, 3)):
+        got, cnt = run(dets[0], [img], 12, 9, 32, 3, pitch=pitch, offset=offset)
+        assert_parity(got, cnt, [img], 12, 9, 32, 3, 0)
+
+
+@pytest.mark.parametrize("thresh,arc,cell", [(0, 9, 32), (1, 16, 32), (255, 9, 32), (254, 9, 64),
+                                             (30, 12, 96), (15, 13, 160), (5, 10, 32)])
+def test_parameter_edges(dets, thresh, arc, cell):
+    img = synth.make_frame(640, 480, seed=thresh + arc, n_shapes=40)
+    modes = (0, 1) if thresh == 0 else (0, 1, 2)
+    for mode in modes:
+        got, cnt = run(dets[mode], [img], thresh, arc, cell, 3)
+        assert_parity(got, cnt, [img], thresh, arc, cell, 3, mode)
+
+
+def test_degenerate_frames(dets):
+    flat = np.full((64, 96), 77, dtype=np.uint8)
+    checker = ((np.indices((64, 64)).sum(axis=0) % 2) * 255).astype(np.uint8)
+    dot = np.zeros((7, 7), dtype=np.uint8)
+    dot[3, 3] = 250
+    plateau = np.zeros((40, 40), dtype=np.uint8)
+    plateau[10:30, 10:30] = 200  # a square: equal-score corners and ties
+    for img in (flat, checker, dot, plateau):
+        for mode in (0, 1, 2):
+            got, cnt = run(dets[mode], [img], 10, 9, 32, 1)
+            assert_parity(got, cnt, [img], 10, 9, 32, 1, mode)
+    got, cnt = run(dets[0], [flat], 0, 9, 32, 3)
+    assert cnt[0] == 0 and (got[0][:, 2] == -1).all()
+
+
+# ---- invariance across launch forms ------------------------------------------
+
+def test_every_tile_variant_is_identical(dets, mixed):
+    imgs = mixed[::8]
+    ref, ref_cnt = run(dets[0], imgs, 15, 9, 32, 3)
+    frames = [to_gpu(im) for im in imgs]
+    for v in range(len(vio.variants())):
+        dets[0].set_variant(v)
+        outs, counts = dets[0].detect(frames, 15, 9, 32, 3)
+        dets[0].sync()
+        for a, b in zip(outs, ref):
+            assert np.array_equal(a.cpu().numpy(), b), v
+        assert np.array_equal(counts.cpu().numpy(), ref_cnt)
+    dets[0].set_variant(None)
+    assert_parity(ref, ref_cnt, imgs, 15, 9, 32, 3, 0)
+
+
+def test_graphs_off_and_autotune_identical(mixed):
+    imgs = mixed[::4]
+    a = vio.Detector(max_frames=64, use_graphs=False)
+    b = vio.Detector(max_frames=64, autotune=True)
+    ra, ca = run(a, imgs, 15, 9, 32, 3)
+    rb, cb = run(b, imgs, 15, 9, 32, 3)
+    for x, y in zip(ra, rb):
+        assert np.array_equal(x, y)
+    assert np.array_equal(ca, cb)
+    assert_parity(ra, ca, imgs, 15, 9, 32, 3, 0)
+    a.close()
+    b.close()
+
+
+def test_repeated_calls_and_shape_changes(dets, mixed):
+    """Keys are cleared by each call; alternating shapes reuse plans."""
+    seq = [(mixed[0:3], 3), (mixed[20:21], 2), (mixed[0:3], 3), (mixed[40:48], 1), (mixed[20:21], 2)]
+    for imgs, levels in seq:
+        got, cnt = run(dets[0], imgs, 15, 9, 32, levels)
+        assert_parity(got, cnt, imgs, 15, 9, 32, levels, 0)
+
+
+def test_host_path_matches(dets, mixed):
+    imgs = mixed[::6]
+    outs, counts = dets[0].detect_host(imgs, 15, 9, 32, 3)
+    assert_parity(outs, counts, imgs, 15, 9, 32, 3, 0)
+    # non-contiguous host rows (pitch > w)
+    big = np.zeros((480, 800), dtype=np.uint8)
+    big[:, :752] = mixed[16]
+    outs, counts = dets[0].detect_host([big[:, :752]], 15, 9, 32, 3)
+    assert_parity(outs, counts, [mixed[16]], 15, 9, 32, 3, 0)
+
+
+def test_invalid_arguments_rejected(dets):
+    img = to_gpu(synth.make_frame(64, 64, seed=1))
+    d = dets[0]
+    bad = [dict(thresh=-1), dict(thresh=256), dict(arc_len=8), dict(arc_len=17), dict(cell=0),
+           dict(cell=48), dict(levels=0), dict(levels=6), dict(levels=4)]  # 64>>3 = 8 ok, 64>>4 < 7
+    base = dict(thresh=10, arc_len=9, cell=32, levels=1)
+    for b in bad[:-1]:
+        kw = {**base, **b}
+        with pytest.raises(vio.VioError) as e:
+            d.detect([img], kw["thresh"], kw["arc_len"], kw["cell"], kw["levels"])
+        assert e.value.status == 1, b
+    d.detect([img], 10, 9, 32, 4)  # 8x8 smallest level is fine
+    with pytest.raises(vio.VioError):
+        d.detect([img], 10, 9, 32, 5)
+    with pytest.raises(vio.VioError):
+        dets[2].detect([img], 0, 9, 32, 1)  # MT needs thresh >= 1
+    small = to_gpu(np.zeros((6, 30), dtype=np.uint8))
+    with pytest.raises(vio.VioError):
+        d.detect([small], 10, 9, 32, 1)
+    d.sync()
+
+
+def test_budget_exceeded_reports_oom(mixed):
+    d = vio.Detector(max_frames=64, mem_budget_bytes=1 << 20)
+    frames = [to_gpu(im) for im in mixed[48:64]]
+    with pytest.raises(vio.VioError) as e:
+        d.detect(frames, 15, 9, 32, 3)
+    assert e.value.status == 2
+    # a small request still fits the budget afterwards
+    outs, counts = d.detect([to_gpu(mixed[0])], 15, 9, 32, 1)
+    d.sync()
+    want, n = oracle.detect(mixed[0], 15, 9, 32, 1)
+    assert np.array_equal(outs[0].cpu().numpy(), want)
+    d.close()
