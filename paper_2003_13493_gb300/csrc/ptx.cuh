@@ -61,6 +61,14 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// A tensor map that the host rewrote in global memory since an earlier
+// kernel used that address may still sit in the tensor-map cache: acquire
+// it through the tensormap proxy before the first copy that uses it.
+__device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 // TMA: copies the box at element coordinates (x, y) of a 2D tensor map into
 // shared memory and signals `bar` with the byte count.  x * element size
 // must be a multiple of 16.

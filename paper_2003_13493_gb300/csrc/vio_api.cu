@@ -281,19 +281,23 @@ vio_status enqueue_kernels(vio_ctx* ctx, const Plan& p, cudaStream_t s) {
     auto* fds = reinterpret_cast<const FrameDesc*>(ctx->d_call + ctx->layout.fds);
     auto* maps0 = reinterpret_cast<const CUtensorMap*>(ctx->d_call + ctx->layout.maps0);
     const bool prof = ctx->cfg.profile != 0;
-    if (prof) VIO_CK(cudaEventRecord(ctx->stage_ev[0], s));
+    // inside stream capture only an external record becomes a graph node
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (prof) VIO_CK(cudaStreamIsCapturing(s, &cap));
+    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[0], s, rec_flags));
     if (p.levels > 1) {
         pyr_fn(p.levels)<<<p.pyr_blocks, 256, 0, s>>>(hdr, fds, p.d_block_start);
         VIO_CK(cudaGetLastError());
     }
-    if (prof) VIO_CK(cudaEventRecord(ctx->stage_ev[1], s));
+    if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[1], s, rec_flags));
     v.fn[p.mode]<<<p.grid, 256, v.smem, s>>>(hdr, fds, maps0, p.d_mapsk, p.d_items, ctx->d_counter,
                                              ctx->d_status);
     VIO_CK(cudaGetLastError());
-    if (prof) VIO_CK(cudaEventRecord(ctx->stage_ev[2], s));
+    if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[2], s, rec_flags));
     decode_kernel<<<p.n, 256, 0, s>>>(hdr, fds, ctx->d_counter);
     VIO_CK(cudaGetLastError());
-    if (prof) VIO_CK(cudaEventRecord(ctx->stage_ev[3], s));
+    if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[3], s, rec_flags));
     return VIO_OK;
 }
 

@@ -262,6 +262,7 @@ __global__ void __launch_bounds__(256) fast_nms_cell_kernel(
         const int x0 = wi.tx * TW, y0 = wi.ty * TH;
         if (tid == 0) {
             const CUtensorMap* map = k == 0 ? &maps0[wi.frame] : &mapsk[wi.frame * (kMaxLevels - 1) + k - 1];
+            fence_tensormap_acquire(map);
             mbar_arrive_expect_tx(&bar, G::BOX);
             tma_load_2d(img, map, &bar, x0 - 16, y0 - 4);
         }

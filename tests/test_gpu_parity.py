@@ -221,3 +221,24 @@ def test_budget_exceeded_reports_oom(mixed):
     want, n = oracle.detect(mixed[0], 15, 9, 32, 1)
     assert np.array_equal(outs[0].cpu().numpy(), want)
     d.close()
+
+
+def test_alternating_buffers_and_variants(dets):
+    """Same batch shape, different frame buffers (and contents) and tile
+    variants call after call: every call must read its own frames through
+    freshly written tensor maps."""
+    a = [synth.make_frame(640, 480, seed=500 + i, n_shapes=30) for i in range(3)]
+    b = [synth.make_frame(640, 480, seed=600 + i, n_shapes=30) for i in range(3)]
+    ga = [to_gpu(im) for im in a]
+    gb = [to_gpu(im) for im in b]
+    want_a = [oracle.detect(im, 15, 9, 32, 3)[0] for im in a]
+    want_b = [oracle.detect(im, 15, 9, 32, 3)[0] for im in b]
+    nv = len(vio.variants())
+    for rep in range(3 * nv):
+        dets[0].set_variant(rep % nv if rep >= nv else None)
+        imgs, want = (ga, want_a) if rep % 2 == 0 else (gb, want_b)
+        outs, _ = dets[0].detect(imgs, 15, 9, 32, 3)
+        dets[0].sync()
+        for o, w in zip(outs, want):
+            assert np.array_equal(o.cpu().numpy(), w), rep
+    dets[0].set_variant(None)
