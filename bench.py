@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/profile legs")
     ap.add_argument("--spin", type=float, default=0.5, help="seconds of untimed steps before timing")
+    ap.add_argument("--variant", type=int, default=-1, help="pin a tile variant instead of autotuning")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the Poisson serving run (0 skips it)")
     return ap.parse_args()
 
 
@@ -120,9 +123,11 @@ class ClockSampler:
 # ---- ncu traffic recorded for the current kernel source ------------------------
 
 def kernel_source_hash() -> str:
+    import glob
+
     h = hashlib.sha256()
-    for rel in ("paper_2003_13493_gb300/csrc/vio_kernels.cuh", "paper_2003_13493_gb300/csrc/ptx.cuh"):
-        with open(os.path.join(ROOT, rel), "rb") as f:
+    for path in sorted(glob.glob(os.path.join(ROOT, "paper_2003_13493_gb300", "csrc", "*.cuh"))):
+        with open(path, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -213,7 +218,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     sh = ctypes.c_void_p(stream.cuda_stream)
 
-    det = vio.Detector(device=local_rank, max_frames=max(64, n), autotune=True)
+    det = vio.Detector(device=local_rank, max_frames=max(64, n), autotune=args.variant < 0)
+    if args.variant >= 0:
+        det.set_variant(args.variant)
     dev_sets = []
     with torch.cuda.stream(stream):
         for _ in range(sets):
@@ -286,7 +293,8 @@ def run_ours(args, rank, world, local_rank):
                    "arc_len": wl["arc"], "cell": wl["cell"], "score": "SAD-B",
                    "l2": f"inputs rotate over {sets} device copies of the batch "
                          f"({sets * mpx:.0f} MB > 129 MB L2)",
-                   "tile": {"w": tune[0], "h": tune[1], "variant": tune[2], "picked_by": "autotuner"},
+                   "tile": {"w": tune[0], "h": tune[1], "variant": tune[2],
+                            "picked_by": "autotuner" if args.variant < 0 else "--variant"},
                    "parallelism": f"replicas x{world}, no collective"},
         "clocks": clk,
         "gpu_launches": args.steps * (3 if wl["levels"] > 1 else 2),
@@ -382,10 +390,89 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
                   "d2h_bytes_per_step": d2h, "steps": esteps,
                   "what": "vio_detect_host: pinned host frames -> device -> detect -> host cells, synchronous"}
 
+    if args.serve_seconds > 0:
+        out["serving"] = serving_leg(args, dev.index)
+
     if not args.no_cpu_baseline:
         rate, cores, sample = oracle_rate(frames_np, wl, args.cpu_seconds)
         out["cpu_baseline"] = {"value": round(rate, 2), "unit": "frames/s", "cores": cores, "kind": "oracle",
                                "sample": sample}
+    return out
+
+
+def serving_leg(args, dev_index: int) -> dict:
+    """Serving workload: 16 camera streams with Poisson arrivals at
+    200 + 800 s/15 Hz (stream s), resolutions cycling through the four mixed
+    sizes, 4 seeded frames per stream, 3 levels, FAST-9, thresh 15, 32x32
+    cells, 4 GiB device budget.  Latency = submit -> cells in host memory.
+    The same arrival schedule is replayed against a one-frame-per-launch
+    server (1 lane, batch 1) for comparison."""
+    import numpy as np
+    import torch
+
+    from paper_2003_13493_gb300 import synth, vio
+
+    n_streams, per_stream, T = 16, 4, args.serve_seconds
+    pools = []
+    for s in range(n_streams):
+        w, h = synth.MIXED_SIZES[s % 4]
+        pools.append([torch.from_numpy(synth.make_frame(w, h, seed=5000 + 16 * s + j)).pin_memory()
+                      for j in range(per_stream)])
+    dims = [[vio.Dims(p.shape[1], p.shape[0], p.shape[1]) for p in pool] for pool in pools]
+    rng = np.random.default_rng(4)
+    events = []
+    for s in range(n_streams):
+        lam = 200.0 + 800.0 * s / (n_streams - 1)
+        t = rng.exponential(1.0 / lam)
+        j = 0
+        while t < T:
+            events.append((t, s, j % per_stream))
+            t += rng.exponential(1.0 / lam)
+            j += 1
+    events.sort()
+
+    def run(**kw):
+        det = vio.Detector(device=dev_index, max_frames=max(64, kw.get("max_batch", 1)))
+        det.serve_start(thresh=15, arc_len=9, cell_size=32, levels=3, keep_results=0,
+                        mem_budget_bytes=4 << 30, queue_capacity=1 << 20, **kw)
+        # warm the lanes (graphs, arenas) outside the measured window
+        for s in range(n_streams):
+            det.submit_raw(s, pools[s][0].data_ptr(), dims[s][0])
+        det.drain(120000)
+        det.serve_stop()
+        det.serve_start(thresh=15, arc_len=9, cell_size=32, levels=3, keep_results=0,
+                        mem_budget_bytes=4 << 30, queue_capacity=1 << 20, **kw)
+        lag = 0.0
+        rejected = 0
+        t0 = time.perf_counter()
+        for (t, s, j) in events:
+            while True:
+                now = time.perf_counter() - t0
+                if now >= t:
+                    break
+            lag = max(lag, now - t)
+            st, _ = det.submit_raw(s, pools[s][j].data_ptr(), dims[s][j])
+            rejected += st != 0
+        det.drain(600000)
+        stats = det.serve_stats()
+        det.serve_stop()
+        det.close()
+        stats["max_submit_lag_us"] = round(lag * 1e6, 1)
+        stats["rejected"] = rejected
+        return stats
+
+    served = run(max_batch=32, lanes=3, max_wait_us=0)
+    plain = run(max_batch=1, lanes=1, max_wait_us=0)
+    offered = len(events) / T
+    out = {"value": round(served["frames_per_s"], 1), "unit": "frames/s", "offered_fps": round(offered, 1),
+           "frames": len(events), "p50_us": round(served["p50_us"], 1), "p99_us": round(served["p99_us"], 1),
+           "max_us": round(served["max_us"], 1), "mean_batch": round(served["mean_batch"], 2),
+           "max_submit_lag_us": served["max_submit_lag_us"], "lanes": 3, "max_batch": 32,
+           "plain": {"value": round(plain["frames_per_s"], 1), "p50_us": round(plain["p50_us"], 1),
+                     "p99_us": round(plain["p99_us"], 1), "max_us": round(plain["max_us"], 1),
+                     "what": "same arrivals, one frame per launch on one lane"},
+           "what": f"{n_streams} Poisson camera streams (200..1000 Hz) for {T:g} s, 4 GiB budget, "
+                   "latency from submit to cells in host memory"}
     return out
 
 

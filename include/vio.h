@@ -185,6 +185,66 @@ vio_status vio_set_tuning(vio_ctx* ctx, const vio_tuning* t);
 int vio_num_variants(void);
 vio_status vio_variant(int i, vio_tuning* out);
 
+/* CUDA device ordinal of the context, or -1 for NULL. */
+int vio_device(const vio_ctx* ctx);
+
+/*
+ * Serving: frames of many camera streams and sizes are submitted one by one
+ * from host memory; a scheduler thread owned by the context batches the
+ * pending frames into the next free lane (a CUDA stream with its own
+ * resident buffers), so frames that arrive while other batches are on the
+ * GPU are admitted as soon as a lane and device memory free up, and batches
+ * on different lanes overlap on the device.  Every frame's result is the
+ * same as a vio_detect of that frame alone.
+ */
+typedef struct {
+    int thresh, arc_len, cell_size, levels; /* detection parameters, as vio_detect          */
+    int max_batch;          /* most frames per launch (1..1024)                             */
+    int max_wait_us;        /* a partial batch waits until its oldest frame is this old      */
+    int lanes;              /* launches in flight at once, one CUDA stream each (1..8)       */
+    size_t mem_budget_bytes;/* device bytes for the frames in flight (inputs, pyramid, keys, */
+                            /* cells); 0 = unbounded                                         */
+    int queue_capacity;     /* pending frames before vio_submit returns VIO_ERR_BUSY         */
+    int keep_results;       /* 1 = keep each result until vio_poll takes it; 0 = stats only  */
+} vio_serve_config;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, batches;
+    double mean_batch;      /* frames per launch                                             */
+    double p50_us, p99_us, max_us, mean_us; /* submit -> cells in host memory, per frame      */
+    double frames_per_s;    /* completed frames / (last completion - first submit)           */
+} vio_serve_stats_t;
+
+/* Defaults: thresh 15, arc 9, cell 32, levels 3, batch 32, no wait, 3 lanes,
+ * 4 GiB budget, 65536 queue slots, results kept. */
+void vio_serve_config_default(vio_serve_config* cfg);
+
+/* Starts the scheduler thread of ctx.  VIO_ERR_BUSY if already serving. */
+vio_status vio_serve_start(vio_ctx* ctx, const vio_serve_config* cfg);
+
+/* Queues one frame.  host_frame must stay valid and unchanged until the
+ * frame completes (pinned memory lets its copy overlap other work).
+ * *ticket identifies the frame for vio_poll.  Errors: VIO_ERR_INVALID_ARG
+ * (not serving, bad dims), VIO_ERR_BUSY (queue full), VIO_ERR_OOM (frame
+ * larger than the budget), or the scheduler's own error. */
+vio_status vio_submit(vio_ctx* ctx, int stream_id, const uint8_t* host_frame, vio_dims dims, uint64_t* ticket);
+
+/* *done = 1 and the frame's cells (vio_num_cells records) and non-empty
+ * count copied out when the frame has completed (the result is then
+ * released); *done = 0 otherwise.  host_out / count may be NULL.
+ * VIO_ERR_NOT_FOUND for a ticket never issued or already taken. */
+vio_status vio_poll(vio_ctx* ctx, uint64_t ticket, vio_feature* host_out, int32_t* count, int* done);
+
+/* Waits until every submitted frame has completed (VIO_ERR_TIMEOUT after
+ * timeout_ms). */
+vio_status vio_serve_drain(vio_ctx* ctx, int timeout_ms);
+
+/* Counters and latency percentiles of the frames completed so far. */
+vio_status vio_serve_stats(vio_ctx* ctx, vio_serve_stats_t* out);
+
+/* Finishes the queued frames, stops the scheduler, frees the lanes. */
+vio_status vio_serve_stop(vio_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

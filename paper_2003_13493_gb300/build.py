@@ -15,7 +15,6 @@ NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
     "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-    "-shared",
 ]
 
 
@@ -34,17 +33,34 @@ def nvcc() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles the library when a source is newer than it; returns its path."""
+    """Compiles the library when a source is newer than it; returns its path.
+    Translation units compile in parallel, then one link step."""
+    from concurrent.futures import ThreadPoolExecutor
+
     os.makedirs(OUT_DIR, exist_ok=True)
     if not force and os.path.exists(LIB_PATH):
         t = os.path.getmtime(LIB_PATH)
         if all(os.path.getmtime(p) <= t for p in _deps()):
             return LIB_PATH
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp, *_sources()]
+    pid = os.getpid()
+    objs = [os.path.join(OUT_DIR, os.path.basename(src) + f".{pid}.o") for src in _sources()]
+
+    def compile_one(args):
+        src, obj = args
+        cmd = [nvcc(), *NVCC_FLAGS, "-c", "-I", INCLUDE, "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+
+    with ThreadPoolExecutor(max(1, len(objs))) as ex:
+        list(ex.map(compile_one, zip(_sources(), objs)))
+    tmp = LIB_PATH + f".tmp{pid}"
+    link = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
     if verbose:
-        print(" ".join(cmd))
-    subprocess.check_call(cmd)
+        print(" ".join(link))
+    subprocess.check_call(link)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 

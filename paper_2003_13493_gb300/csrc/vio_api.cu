@@ -1,10 +1,11 @@
 // Host runtime behind include/vio.h: argument checks, resident buffers, the
-// per-shape plan (work list, pyramid layout, tensor maps), CUDA-graph replay
+// per-call block (frame descriptors, tensor maps, tile table), CUDA-graph replay
 // and the tile autotuner.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -23,26 +24,22 @@ namespace {
 // ---------------------------------------------------------------------------
 // Built variants of the fused kernel.
 // ---------------------------------------------------------------------------
-using DetectFn = void (*)(const CallHeader*, const FrameDesc*, const CUtensorMap*, const CUtensorMap*,
-                          const WorkItem*, int32_t*, uint32_t*);
-using PyrFn = void (*)(const CallHeader*, const FrameDesc*, const int32_t*);
+using DetectFn = void (*)(const uint8_t*, int32_t*, uint32_t*);
+using PyrFn = void (*)(const uint8_t*);
 
 struct Variant {
     int tw, th, smem;
     DetectFn fn[3];
 };
 
-template <int TW, int TH>
+template <int TH>
 Variant make_variant() {
-    return Variant{TW, TH, TileGeom<TW, TH>::SMEM,
-                   {fast_nms_cell_kernel<TW, TH, 0>, fast_nms_cell_kernel<TW, TH, 1>,
-                    fast_nms_cell_kernel<TW, TH, 2>}};
+    return Variant{TileGeom<TH>::TW, TH, TileGeom<TH>::SMEM,
+                   {fast_nms_cell_kernel<TH, 0>, fast_nms_cell_kernel<TH, 1>, fast_nms_cell_kernel<TH, 2>}};
 }
 
 const std::vector<Variant>& variants() {
-    static const std::vector<Variant> v = {make_variant<128, 32>(), make_variant<64, 32>(),
-                                           make_variant<192, 32>(), make_variant<128, 64>(),
-                                           make_variant<64, 64>()};
+    static const std::vector<Variant> v = {make_variant<62>(), make_variant<30>(), make_variant<126>()};
     return v;
 }
 
@@ -56,22 +53,25 @@ PyrFn pyr_fn(int levels) {
     }
 }
 
+constexpr int kBoxW = 144;  // TMA box width of every variant
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// Layout of the per-call block uploaded before each launch.
-struct CallLayout {
-    size_t hdr = 0, fds = 0, maps0 = 0, bytes = 0;
-    explicit CallLayout(int max_frames) {
-        hdr = 0;
-        fds = align_up(sizeof(CallHeader), 128);
-        maps0 = align_up(fds + sizeof(FrameDesc) * max_frames, 128);
-        bytes = align_up(maps0 + sizeof(CUtensorMap) * max_frames, 128);
-    }
-};
+// Bytes of the largest call block a context can send.
+size_t call_block_cap(int max_frames) {
+    size_t b = align_up(sizeof(CallHeader), 128);
+    b += align_up(sizeof(FrameDesc) * max_frames, 128);
+    b += align_up(sizeof(CUtensorMap) * max_frames, 128);
+    b += align_up(sizeof(CUtensorMap) * max_frames * (kMaxLevels - 1), 128);
+    b += align_up(sizeof(int32_t) * (max_frames * kMaxLevels + 1), 128);
+    b += align_up(sizeof(int32_t) * (max_frames + 1), 128);
+    b += align_up(sizeof(int32_t) * (max_frames + 1), 128);
+    return b;
+}
 
 struct ShapeKey {
     std::vector<int32_t> v;
@@ -104,46 +104,19 @@ struct MapHash {
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------
-struct Plan {
-    ShapeKey key;
-    int variant = 0;
-    int levels = 1, cell = 32, n = 0, mode = 0;
-    int n_items = 0, pyr_blocks = 0, grid = 0;
-    std::vector<int> gw, gh, ncell;
-    std::vector<size_t> key_off;                    // element offset into keys
-    std::vector<std::vector<size_t>> lev_off;       // byte offset into pyramid arena
-    std::vector<std::vector<int>> lev_pitch;
-    size_t keys_total = 0, pyr_total = 0, cells_total = 0;
-    // device data fixed for the plan's lifetime
-    WorkItem* d_items = nullptr;
-    CUtensorMap* d_mapsk = nullptr;     // [n][kMaxLevels-1], resident pyramid levels
-    int32_t* d_block_start = nullptr;   // [n+1] pyramid blocks per frame, prefix sum
-    cudaGraphExec_t graph = nullptr;
-    void release() {
-        if (graph) cudaGraphExecDestroy(graph);
-        cudaFree(d_items);
-        cudaFree(d_mapsk);
-        cudaFree(d_block_start);
-        graph = nullptr;
-        d_items = nullptr;
-        d_mapsk = nullptr;
-        d_block_start = nullptr;
-    }
-};
-
 struct vio_ctx {
     vio_config cfg{};
     int sm_count = 0;
     std::string err;
     EncodeTiledFn encode = nullptr;
-    CallLayout layout{1};
+    size_t call_cap = 0;
 
     // resident device buffers
-    uint8_t* d_call = nullptr;          // CallHeader | FrameDesc[] | maps0[]
-    int32_t* d_counter = nullptr;
-    uint64_t* d_keys = nullptr;
+    uint8_t* d_call = nullptr;          // the current call block
+    int32_t* d_counter = nullptr;       // work-item counter of the fused kernel
+    uint64_t* d_keys = nullptr;         // packed cell keys, zero when idle
     size_t keys_cap = 0;
-    uint8_t* d_pyr = nullptr;
+    uint8_t* d_pyr = nullptr;           // pyramid levels 1..L-1 of every frame
     size_t pyr_cap = 0;
     uint8_t* d_in = nullptr;            // staged level-0 frames (host path / unaligned frames)
     size_t in_cap = 0;
@@ -166,14 +139,21 @@ struct vio_ctx {
     cudaStream_t last_stream = nullptr;
     bool have_last = false;
 
-    std::unordered_map<ShapeKey, Plan, ShapeHash> plans;
-    std::unordered_map<ShapeKey, int, ShapeHash> tuned;  // shape -> variant
+    // one graph per (variant, levels): every batch shape replays it
+    cudaGraphExec_t graphs[8][kMaxLevels + 1] = {};
+    int grid_fused[8] = {};
+    std::unordered_map<ShapeKey, int, ShapeHash> tuned;  // batch shape -> variant
     std::unordered_map<MapKey, CUtensorMap, MapHash> map_cache;
     int pinned_variant = -1;
     int last_variant = 0;
-    void drop_plans() {
-        for (auto& kv : plans) kv.second.release();
-        plans.clear();
+
+    void drop_graphs() {
+        for (auto& row : graphs)
+            for (auto& g : row)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
     }
 };
 
@@ -193,10 +173,12 @@ vio_status fail(vio_ctx* c, vio_status s, const std::string& msg) {
         }                                                                                     \
     } while (0)
 
+// Grows a resident buffer to `need` bytes.  Growing waits for the device
+// (the old buffer may still be in use), so buffers grow geometrically.
 vio_status grow(vio_ctx* ctx, void** p, size_t* cap, size_t need, bool zero) {
     if (need <= *cap && *p) return VIO_OK;
     size_t want = std::max(need, *cap + *cap / 2);
-    size_t budget = ctx->cfg.mem_budget_bytes;
+    const size_t budget = ctx->cfg.mem_budget_bytes;
     if (budget && ctx->bytes_in_use - *cap + want > budget) {
         want = need;
         if (ctx->bytes_in_use - *cap + want > budget)
@@ -231,7 +213,7 @@ vio_status encode_map(vio_ctx* ctx, CUtensorMap* out, const void* ptr, int w, in
                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, VIO_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
-    if (ctx->map_cache.size() > 8192) ctx->map_cache.clear();
+    if (ctx->map_cache.size() > 16384) ctx->map_cache.clear();
     ctx->map_cache.emplace(key, *out);
     return VIO_OK;
 }
@@ -259,14 +241,12 @@ vio_status check_args(vio_ctx* ctx, const void* frames, const vio_dims* dims, in
     return VIO_OK;
 }
 
-ShapeKey shape_key(const vio_dims* dims, int n, int cell, int levels, int mode, int variant) {
+ShapeKey shape_key(const vio_dims* dims, int n, int cell, int levels) {
     ShapeKey k;
-    k.v.reserve(3 * n + 5);
+    k.v.reserve(2 * n + 3);
     k.v.push_back(n);
     k.v.push_back(cell);
     k.v.push_back(levels);
-    k.v.push_back(mode);
-    k.v.push_back(variant);
     for (int i = 0; i < n; ++i) {
         k.v.push_back(dims[i].w);
         k.v.push_back(dims[i].h);
@@ -274,198 +254,183 @@ ShapeKey shape_key(const vio_dims* dims, int n, int cell, int levels, int mode, 
     return k;
 }
 
-// Enqueues pyramid -> fused detect -> decode on `s` for plan p.
-vio_status enqueue_kernels(vio_ctx* ctx, const Plan& p, cudaStream_t s) {
-    const Variant& v = variants()[p.variant];
-    auto* hdr = reinterpret_cast<const CallHeader*>(ctx->d_call + ctx->layout.hdr);
-    auto* fds = reinterpret_cast<const FrameDesc*>(ctx->d_call + ctx->layout.fds);
-    auto* maps0 = reinterpret_cast<const CUtensorMap*>(ctx->d_call + ctx->layout.maps0);
+// Enqueues pyramid -> fused detect -> decode on `s`; launch shapes depend only
+// on the context (the kernels read the batch from the call block).
+vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s) {
+    const Variant& v = variants()[variant];
+    const int mode = ctx->cfg.score;
     const bool prof = ctx->cfg.profile != 0;
     // inside stream capture only an external record becomes a graph node
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (prof) VIO_CK(cudaStreamIsCapturing(s, &cap));
     const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[0], s, rec_flags));
-    if (p.levels > 1) {
-        pyr_fn(p.levels)<<<p.pyr_blocks, 256, 0, s>>>(hdr, fds, p.d_block_start);
+    if (levels > 1) {
+        pyr_fn(levels)<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->d_call);
         VIO_CK(cudaGetLastError());
     }
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[1], s, rec_flags));
-    v.fn[p.mode]<<<p.grid, 256, v.smem, s>>>(hdr, fds, maps0, p.d_mapsk, p.d_items, ctx->d_counter,
-                                             ctx->d_status);
+    if (!ctx->grid_fused[variant]) {
+        int occ = 0;
+        VIO_CK(cudaFuncSetAttribute(v.fn[mode], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
+        VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn[mode], 256, v.smem));
+        ctx->grid_fused[variant] = std::max(1, occ) * ctx->sm_count;
+    }
+    v.fn[mode]<<<ctx->grid_fused[variant], 256, v.smem, s>>>(ctx->d_call, ctx->d_counter, ctx->d_status);
     VIO_CK(cudaGetLastError());
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[2], s, rec_flags));
-    decode_kernel<<<p.n, 256, 0, s>>>(hdr, fds, ctx->d_counter);
+    decode_kernel<<<ctx->sm_count * 4, 256, 0, s>>>(ctx->d_call, ctx->d_counter);
     VIO_CK(cudaGetLastError());
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[3], s, rec_flags));
     return VIO_OK;
 }
 
-// Builds (or finds) the plan for this batch shape and makes the resident
-// buffers large enough for it.
-vio_status get_plan(vio_ctx* ctx, const vio_dims* dims, int n, int cell, int levels, int variant, Plan** out) {
-    const int mode = ctx->cfg.score;
-    ShapeKey key = shape_key(dims, n, cell, levels, mode, variant);
-    auto it = ctx->plans.find(key);
-    Plan* p = nullptr;
-    if (it != ctx->plans.end()) {
-        p = &it->second;
-    } else {
-        Plan np;
-        np.key = key;
-        np.variant = variant;
-        np.levels = levels;
-        np.cell = cell;
-        np.n = n;
-        np.mode = mode;
+vio_status get_graph(vio_ctx* ctx, int variant, int levels, cudaGraphExec_t* out) {
+    cudaGraphExec_t& g = ctx->graphs[variant][levels];
+    if (!g) {
+        // the launch attributes are set outside the capture
         const Variant& v = variants()[variant];
-        std::vector<WorkItem> items;
-        std::vector<int32_t> bstart(n + 1, 0);
-        size_t koff = 0, poff = 0, coff = 0;
-        np.lev_off.resize(n);
-        np.lev_pitch.resize(n);
-        for (int i = 0; i < n; ++i) {
-            const int w = dims[i].w, h = dims[i].h;
-            const int gw = (w + cell - 1) / cell, gh = (h + cell - 1) / cell;
-            np.gw.push_back(gw);
-            np.gh.push_back(gh);
-            np.ncell.push_back(gw * gh);
-            np.key_off.push_back(koff);
-            koff += align_up((size_t)gw * gh, 16);
-            coff += (size_t)gw * gh;
-            np.lev_off[i].assign(kMaxLevels, 0);
-            np.lev_pitch[i].assign(kMaxLevels, 0);
-            for (int k = 1; k < levels; ++k) {
-                const int wk = w >> k, hk = h >> k;
-                const int pk = (int)align_up(wk, 128);
-                np.lev_off[i][k] = poff;
-                np.lev_pitch[i][k] = pk;
-                poff += align_up((size_t)pk * hk, 256);
-            }
-            const int B = 1 << (levels - 1);
-            const int bx = ((w + B - 1) / B + 31) / 32, by = ((h + B - 1) / B + 7) / 8;
-            bstart[i + 1] = bstart[i] + (levels > 1 ? bx * by : 0);
-        }
-        // work list: level-major, then frame, then tile rows
-        for (int k = 0; k < levels; ++k)
-            for (int i = 0; i < n; ++i) {
-                const int wk = dims[i].w >> k, hk = dims[i].h >> k;
-                const int ntx = (wk + v.tw - 1) / v.tw, nty = (hk + v.th - 1) / v.th;
-                for (int ty = 0; ty < nty; ++ty)
-                    for (int tx = 0; tx < ntx; ++tx)
-                        items.push_back(WorkItem{(uint16_t)i, (uint8_t)k, 0, (uint16_t)tx, (uint16_t)ty});
-            }
-        np.n_items = (int)items.size();
-        np.pyr_blocks = bstart[n];
-        np.keys_total = koff;
-        np.pyr_total = poff;
-        np.cells_total = coff;
-
-        // resident buffers (keys are zero when allocated and cleared by decode);
-        // growing them moves the arenas, which invalidates every other plan
-        vio_status st;
-        const void* keys0 = ctx->d_keys;
-        const void* pyr0 = ctx->d_pyr;
-        if ((st = grow(ctx, (void**)&ctx->d_keys, &ctx->keys_cap, np.keys_total * 8, true)) != VIO_OK) return st;
-        if ((st = grow(ctx, (void**)&ctx->d_pyr, &ctx->pyr_cap, std::max<size_t>(np.pyr_total, 256), false)) != VIO_OK)
-            return st;
-        if (keys0 != ctx->d_keys || pyr0 != ctx->d_pyr || ctx->plans.size() >= 64) {
-            VIO_CK(cudaDeviceSynchronize());
-            ctx->drop_plans();
-        }
-        int occ = 0;
-        VIO_CK(cudaFuncSetAttribute(v.fn[mode], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
-        VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn[mode], 256, v.smem));
-        np.grid = std::max(1, std::min(occ, 8)) * ctx->sm_count;
-        np.grid = std::min(np.grid, std::max(1, np.n_items));
-        // tensor maps for levels >= 1 (resident pyramid, fixed per plan)
-        std::vector<CUtensorMap> mapsk((size_t)n * (kMaxLevels - 1));
-        for (int i = 0; i < n; ++i)
-            for (int k = 1; k < levels; ++k) {
-                if ((st = encode_map(ctx, &mapsk[(size_t)i * (kMaxLevels - 1) + k - 1], ctx->d_pyr + np.lev_off[i][k],
-                                     dims[i].w >> k, dims[i].h >> k, np.lev_pitch[i][k], v.tw + 32, v.th + 8)) !=
-                    VIO_OK)
-                    return st;
-            }
-        auto upload = [&](void** dst, const void* src, size_t bytes) -> vio_status {
-            VIO_CK(cudaMalloc(dst, std::max<size_t>(bytes, 16)));
-            VIO_CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
-            return VIO_OK;
-        };
-        if ((st = upload((void**)&np.d_items, items.data(), items.size() * sizeof(WorkItem))) != VIO_OK ||
-            (st = upload((void**)&np.d_mapsk, mapsk.data(), mapsk.size() * sizeof(CUtensorMap))) != VIO_OK ||
-            (st = upload((void**)&np.d_block_start, bstart.data(), bstart.size() * sizeof(int32_t))) != VIO_OK) {
-            np.release();
-            return st;
-        }
-        p = &ctx->plans.emplace(key, std::move(np)).first->second;
-        if (ctx->cfg.use_graphs) {
-            cudaGraph_t g = nullptr;
-            VIO_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-            vio_status es = enqueue_kernels(ctx, *p, ctx->capture_stream);
-            cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &g);
-            if (es != VIO_OK) return es;
-            VIO_CK(ce);
-            VIO_CK(cudaGraphInstantiate(&p->graph, g, 0));
-            cudaGraphDestroy(g);
-        }
+        VIO_CK(cudaFuncSetAttribute(v.fn[ctx->cfg.score], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
+        cudaGraph_t graph = nullptr;
+        VIO_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        vio_status es = enqueue_kernels(ctx, variant, levels, ctx->capture_stream);
+        cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        if (es != VIO_OK) return es;
+        VIO_CK(ce);
+        VIO_CK(cudaGraphInstantiate(&g, graph, 0));
+        cudaGraphDestroy(graph);
     }
-    *out = p;
+    *out = g;
     return VIO_OK;
 }
 
-// Fills and uploads the call block, then launches the plan on `s`.
-vio_status launch(vio_ctx* ctx, Plan& p, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims,
-                  int thresh, int arc, int4* const* outs, int32_t* counts, cudaStream_t s) {
-    const Variant& v = variants()[p.variant];
-    const int n = p.n;
+// Lays the batch out in the resident arenas, fills the call block, uploads
+// it and launches the three kernels on `s`.
+vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims,
+                  int n, int thresh, int arc, int cell, int levels, int4* const* outs, int32_t* counts,
+                  cudaStream_t s) {
+    const Variant& v = variants()[variant];
+    // arena layout
+    size_t koff = 0, poff = 0;
+    std::vector<size_t> key_off(n);
+    std::vector<std::array<size_t, kMaxLevels>> lev_off(n);
+    std::vector<std::array<int, kMaxLevels>> lev_pitch(n);
+    for (int i = 0; i < n; ++i) {
+        key_off[i] = koff;
+        koff += align_up(vio_num_cells(dims[i].w, dims[i].h, cell), 16);
+        for (int k = 1; k < levels; ++k) {
+            const int wk = dims[i].w >> k, hk = dims[i].h >> k;
+            lev_pitch[i][k] = (int)align_up(wk, 128);
+            lev_off[i][k] = poff;
+            poff += align_up((size_t)lev_pitch[i][k] * hk, 256);
+        }
+    }
+    vio_status st;
+    const void* keys0 = ctx->d_keys;
+    const void* pyr0 = ctx->d_pyr;
+    if ((st = grow(ctx, (void**)&ctx->d_keys, &ctx->keys_cap, koff * 8, true)) != VIO_OK) return st;
+    if ((st = grow(ctx, (void**)&ctx->d_pyr, &ctx->pyr_cap, std::max<size_t>(poff, 256), false)) != VIO_OK) return st;
+    if (keys0 != ctx->d_keys || pyr0 != ctx->d_pyr) ctx->map_cache.clear();
+
     // order against work of this context on another stream
     if (ctx->have_last && ctx->last_stream != s) VIO_CK(cudaStreamWaitEvent(s, ctx->last_ev, 0));
-    // next staging slot
     const int slot = ctx->ring_pos;
     ctx->ring_pos = (ctx->ring_pos + 1) % ctx->ring;
     VIO_CK(cudaEventSynchronize(ctx->ring_ev[slot]));
-    uint8_t* st = ctx->h_stage + (size_t)slot * ctx->layout.bytes;
-    CallHeader* hdr = reinterpret_cast<CallHeader*>(st + ctx->layout.hdr);
-    FrameDesc* fds = reinterpret_cast<FrameDesc*>(st + ctx->layout.fds);
-    CUtensorMap* maps0 = reinterpret_cast<CUtensorMap*>(st + ctx->layout.maps0);
+    uint8_t* st_base = ctx->h_stage + (size_t)slot * ctx->call_cap;
+
+    // call block sections
+    size_t off = align_up(sizeof(CallHeader), 128);
+    const size_t off_fds = off;
+    off += align_up(sizeof(FrameDesc) * n, 128);
+    const size_t off_maps0 = off;
+    off += align_up(sizeof(CUtensorMap) * n, 128);
+    const size_t off_mapsk = off;
+    off += align_up(sizeof(CUtensorMap) * n * (kMaxLevels - 1), 128);
+    const size_t off_tiles = off;
+    off += align_up(sizeof(int32_t) * (n * levels + 1), 128);
+    const size_t off_blocks = off;
+    off += align_up(sizeof(int32_t) * (n + 1), 128);
+    const size_t off_cells = off;
+    off += align_up(sizeof(int32_t) * (n + 1), 128);
+    const size_t bytes = off;
+
+    CallHeader* hdr = reinterpret_cast<CallHeader*>(st_base);
+    FrameDesc* fds = reinterpret_cast<FrameDesc*>(st_base + off_fds);
+    CUtensorMap* maps0 = reinterpret_cast<CUtensorMap*>(st_base + off_maps0);
+    CUtensorMap* mapsk = reinterpret_cast<CUtensorMap*>(st_base + off_mapsk);
+    int32_t* tiles = reinterpret_cast<int32_t*>(st_base + off_tiles);
+    int32_t* blocks = reinterpret_cast<int32_t*>(st_base + off_blocks);
+    int32_t* cells = reinterpret_cast<int32_t*>(st_base + off_cells);
     std::memset(hdr, 0, sizeof(CallHeader));
     hdr->thresh = thresh;
     hdr->arc = arc;
     hdr->n_frames = n;
-    hdr->n_items = p.n_items;
-    hdr->mode = p.mode;
-    hdr->cell = p.cell;
-    hdr->levels = p.levels;
+    hdr->levels = levels;
+    hdr->cell = cell;
+    hdr->tile_h = v.th;
     hdr->counts = counts;
+    hdr->off_fds = (uint32_t)off_fds;
+    hdr->off_maps0 = (uint32_t)off_maps0;
+    hdr->off_mapsk = (uint32_t)off_mapsk;
+    hdr->off_tiles = (uint32_t)off_tiles;
+    hdr->off_blocks = (uint32_t)off_blocks;
+    hdr->off_cells = (uint32_t)off_cells;
+    for (int k = 0; k < levels; ++k) {
+        const uint64_t d = (uint64_t)(cell >> k);  // >= 2: cell is a multiple of 32, k <= 4
+        hdr->cell_magic[k] = (uint32_t)(((1ull << 32) + d - 1) / d);
+    }
+    const int B = 1 << (levels - 1);
+    blocks[0] = 0;
+    cells[0] = 0;
     for (int i = 0; i < n; ++i) {
         FrameDesc& f = fds[i];
         std::memset(&f, 0, sizeof(FrameDesc));
         f.w = dims[i].w;
         f.h = dims[i].h;
-        f.gw = p.gw[i];
-        f.gh = p.gh[i];
-        const int B = 1 << (p.levels - 1);
-        f.pyr_bx = ((f.w + B - 1) / B + 31) / 32;
-        f.keys = ctx->d_keys + p.key_off[i];
+        f.gw = (f.w + cell - 1) / cell;
+        f.gh = (f.h + cell - 1) / cell;
+        // pyramid CTAs cover 512 columns x 8B rows of level 0
+        f.pyr_bx = (f.w + 511) / 512;
+        const int pyr_by = (f.h + 8 * B - 1) / (8 * B);
+        blocks[i + 1] = blocks[i] + (levels > 1 ? f.pyr_bx * pyr_by : 0);
+        cells[i + 1] = cells[i] + f.gw * f.gh;
+        f.keys = ctx->d_keys + key_off[i];
         f.out = outs[i];
         f.lev[0] = const_cast<uint8_t*>(lev0[i]);
         f.pitch[0] = pitch0[i];
-        for (int k = 1; k < p.levels; ++k) {
-            f.lev[k] = ctx->d_pyr + p.lev_off[i][k];
-            f.pitch[k] = p.lev_pitch[i][k];
+        if ((st = encode_map(ctx, &maps0[i], lev0[i], f.w, f.h, pitch0[i], kBoxW, v.th + 8)) != VIO_OK) return st;
+        for (int k = 1; k < levels; ++k) {
+            f.lev[k] = ctx->d_pyr + lev_off[i][k];
+            f.pitch[k] = lev_pitch[i][k];
+            if ((st = encode_map(ctx, &mapsk[(size_t)i * (kMaxLevels - 1) + k - 1], f.lev[k], f.w >> k, f.h >> k,
+                                 f.pitch[k], kBoxW, v.th + 8)) != VIO_OK)
+                return st;
         }
-        vio_status es = encode_map(ctx, &maps0[i], lev0[i], f.w, f.h, pitch0[i], v.tw + 32, v.th + 8);
-        if (es != VIO_OK) return es;
     }
-    const size_t bytes = ctx->layout.maps0 + sizeof(CUtensorMap) * n;
-    VIO_CK(cudaMemcpyAsync(ctx->d_call, st, bytes, cudaMemcpyHostToDevice, s));
+    // tiles: coarsest level first, entry (L-1-k)*n + f
+    int acc = 0;
+    for (int kk = 0; kk < levels; ++kk) {
+        const int k = levels - 1 - kk;
+        for (int i = 0; i < n; ++i) {
+            tiles[kk * n + i] = acc;
+            const int wk = dims[i].w >> k, hk = dims[i].h >> k;
+            acc += ((wk + v.tw - 1) / v.tw) * ((hk + v.th - 1) / v.th);
+        }
+    }
+    tiles[n * levels] = acc;
+    hdr->n_items = acc;
+    hdr->n_pyr_blocks = blocks[n];
+    hdr->n_cells = cells[n];
+
+    VIO_CK(cudaMemcpyAsync(ctx->d_call, st_base, bytes, cudaMemcpyHostToDevice, s));
     VIO_CK(cudaEventRecord(ctx->ring_ev[slot], s));
-    if (p.graph) {
-        VIO_CK(cudaGraphLaunch(p.graph, s));
-    } else {
-        vio_status es = enqueue_kernels(ctx, p, s);
-        if (es != VIO_OK) return es;
+    if (ctx->cfg.use_graphs) {
+        cudaGraphExec_t g = nullptr;
+        if ((st = get_graph(ctx, variant, levels, &g)) != VIO_OK) return st;
+        VIO_CK(cudaGraphLaunch(g, s));
+    } else if ((st = enqueue_kernels(ctx, variant, levels, s)) != VIO_OK) {
+        return st;
     }
     VIO_CK(cudaEventRecord(ctx->last_ev, s));
     ctx->last_stream = s;
@@ -473,32 +438,23 @@ vio_status launch(vio_ctx* ctx, Plan& p, const uint8_t* const* lev0, const int* 
     return VIO_OK;
 }
 
-int pick_variant(vio_ctx* ctx, const vio_dims* dims, int n, int cell, int levels) {
-    if (ctx->pinned_variant >= 0) return ctx->pinned_variant;
-    ShapeKey k = shape_key(dims, n, cell, levels, ctx->cfg.score, -1);
-    auto it = ctx->tuned.find(k);
-    return it == ctx->tuned.end() ? 0 : it->second;
-}
-
-vio_status autotune(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims, int n,
-                    int thresh, int arc, int cell, int levels, int4* const* outs, int32_t* counts, cudaStream_t s) {
-    ShapeKey k = shape_key(dims, n, cell, levels, ctx->cfg.score, -1);
-    if (ctx->tuned.count(k)) return VIO_OK;
+vio_status autotune(vio_ctx* ctx, const ShapeKey& key, const uint8_t* const* lev0, const int* pitch0,
+                    const vio_dims* dims, int n, int thresh, int arc, int cell, int levels, int4* const* outs,
+                    int32_t* counts, cudaStream_t s) {
     cudaEvent_t e0, e1;
     VIO_CK(cudaEventCreate(&e0));
     VIO_CK(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_v = 0;
-    for (int vi = 0; vi < (int)variants().size(); ++vi) {
-        Plan* p = nullptr;
-        vio_status st = get_plan(ctx, dims, n, cell, levels, vi, &p);
-        if (st != VIO_OK) return st;
-        for (int r = 0; r < 2; ++r)
-            if ((st = launch(ctx, *p, lev0, pitch0, dims, thresh, arc, outs, counts, s)) != VIO_OK) return st;
+    vio_status st = VIO_OK;
+    for (int vi = 0; vi < (int)variants().size() && st == VIO_OK; ++vi) {
+        for (int r = 0; r < 2 && st == VIO_OK; ++r)
+            st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
+        if (st != VIO_OK) break;
         VIO_CK(cudaEventRecord(e0, s));
         const int reps = 5;
-        for (int r = 0; r < reps; ++r)
-            if ((st = launch(ctx, *p, lev0, pitch0, dims, thresh, arc, outs, counts, s)) != VIO_OK) return st;
+        for (int r = 0; r < reps && st == VIO_OK; ++r)
+            st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
         VIO_CK(cudaEventRecord(e1, s));
         VIO_CK(cudaEventSynchronize(e1));
         float ms = 0;
@@ -510,23 +466,29 @@ vio_status autotune(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitch0,
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->tuned[k] = best_v;
-    return VIO_OK;
+    if (st == VIO_OK) ctx->tuned[key] = best_v;
+    return st;
 }
 
 vio_status detect_impl(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims, int n,
                        int thresh, int arc, int cell, int levels, int4* const* outs, int32_t* counts,
                        cudaStream_t s) {
-    if (ctx->cfg.autotune && ctx->pinned_variant < 0) {
-        vio_status st = autotune(ctx, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
-        if (st != VIO_OK) return st;
+    int vi = ctx->pinned_variant;
+    if (vi < 0) {
+        vi = 0;
+        if (ctx->cfg.autotune) {
+            const ShapeKey key = shape_key(dims, n, cell, levels);
+            auto it = ctx->tuned.find(key);
+            if (it == ctx->tuned.end()) {
+                vio_status st = autotune(ctx, key, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
+                if (st != VIO_OK) return st;
+                it = ctx->tuned.find(key);
+            }
+            vi = it->second;
+        }
     }
-    const int vi = pick_variant(ctx, dims, n, cell, levels);
-    Plan* p = nullptr;
-    vio_status st = get_plan(ctx, dims, n, cell, levels, vi, &p);
-    if (st != VIO_OK) return st;
     ctx->last_variant = vi;
-    return launch(ctx, *p, lev0, pitch0, dims, thresh, arc, outs, counts, s);
+    return launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
 }
 
 }  // namespace
@@ -597,7 +559,7 @@ vio_status vio_create(vio_ctx** out, const vio_config* cfg_in) {
     vio_ctx* ctx = new vio_ctx();
     ctx->cfg = cfg;
     ctx->sm_count = prop.multiProcessorCount;
-    ctx->layout = CallLayout(cfg.max_frames);
+    ctx->call_cap = call_block_cap(cfg.max_frames);
     cudaDriverEntryPointQueryResult q;
     void* fnp = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fnp, 12000, cudaEnableDefault, &q) !=
@@ -610,14 +572,14 @@ vio_status vio_create(vio_ctx** out, const vio_config* cfg_in) {
         vio_destroy(ctx);
         return s;
     };
-    if (cudaMalloc(&ctx->d_call, ctx->layout.bytes) != cudaSuccess) return cleanup(VIO_ERR_OOM);
+    if (cudaMalloc(&ctx->d_call, ctx->call_cap) != cudaSuccess) return cleanup(VIO_ERR_OOM);
     if (cudaMalloc(&ctx->d_counter, sizeof(int32_t) * 4) != cudaSuccess) return cleanup(VIO_ERR_OOM);
     if (cudaMemset(ctx->d_counter, 0, sizeof(int32_t) * 4) != cudaSuccess) return cleanup(VIO_ERR_CUDA);
     if (cudaHostAlloc(&ctx->h_status, 64, cudaHostAllocMapped) != cudaSuccess) return cleanup(VIO_ERR_OOM);
     *ctx->h_status = 0;
     if (cudaHostGetDevicePointer((void**)&ctx->d_status, ctx->h_status, 0) != cudaSuccess)
         return cleanup(VIO_ERR_CUDA);
-    if (cudaHostAlloc(&ctx->h_stage, ctx->layout.bytes * ctx->ring, cudaHostAllocDefault) != cudaSuccess)
+    if (cudaHostAlloc(&ctx->h_stage, ctx->call_cap * ctx->ring, cudaHostAllocDefault) != cudaSuccess)
         return cleanup(VIO_ERR_OOM);
     ctx->ring_ev.resize(ctx->ring);
     for (auto& e : ctx->ring_ev) {
@@ -628,16 +590,19 @@ vio_status vio_create(vio_ctx** out, const vio_config* cfg_in) {
         if (cudaEventCreate(&e) != cudaSuccess) return cleanup(VIO_ERR_CUDA);
     if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
         return cleanup(VIO_ERR_CUDA);
-    ctx->bytes_in_use = ctx->layout.bytes;
+    ctx->bytes_in_use = ctx->call_cap;
     *out = ctx;
     return VIO_OK;
 }
 
+int vio_device(const vio_ctx* ctx) { return ctx ? ctx->cfg.device : -1; }
+
 vio_status vio_destroy(vio_ctx* ctx) {
     if (!ctx) return VIO_OK;
+    vio_serve_stop(ctx);  // no-op unless serving
     cudaSetDevice(ctx->cfg.device);
     cudaDeviceSynchronize();
-    ctx->drop_plans();
+    ctx->drop_graphs();
     cudaFree(ctx->d_call);
     cudaFree(ctx->d_counter);
     cudaFree(ctx->d_keys);

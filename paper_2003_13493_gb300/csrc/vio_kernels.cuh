@@ -25,86 +25,148 @@ struct FrameDesc {
     int32_t pad1[3];
 };
 
-// Call-wide scalars, rewritten by the host for every call.
+// Everything one call needs is uploaded as one contiguous block; this header
+// sits at its start and holds the byte offsets of the other sections:
+//   FrameDesc fds[n]
+//   CUtensorMap maps0[n]                    level 0 (the caller's frames)
+//   CUtensorMap mapsk[n][kMaxLevels - 1]    levels 1.. (resident pyramid)
+//   int32 tiles[n * levels + 1]             prefix sums of tiles, coarsest
+//                                           level first: entry (L-1-k)*n + f
+//   int32 blocks[n + 1]                     prefix sums of pyramid blocks
+//   int32 cells[n + 1]                      prefix sums of cells per frame
 struct CallHeader {
-    int32_t thresh, arc, n_frames, n_items;
-    int32_t mode, cell, levels, pad0;
+    int32_t thresh, arc, n_frames, levels;
+    int32_t cell, n_items, n_pyr_blocks, tile_h;
     int32_t* counts;       // device int32[n_frames] or nullptr
-    uint64_t pad1[3];
+    uint32_t off_fds, off_maps0, off_mapsk, off_tiles, off_blocks, off_cells;
+    // cell_magic[k] = ceil(2^32 / (cell >> k)): for level coordinates
+    // x < 2^16, umulhi(x, magic) == x / (cell >> k) == (x << k) / cell exactly
+    uint32_t cell_magic[kMaxLevels];
+    int32_t n_cells;       // cells of all frames
+    uint64_t pad1;
 };
 
-struct WorkItem {
-    uint16_t frame;
-    uint8_t level;
-    uint8_t pad;
-    uint16_t tx, ty;
+struct CallView {
+    const CallHeader* h;
+    const FrameDesc* fds;
+    const CUtensorMap* maps0;
+    const CUtensorMap* mapsk;
+    const int32_t* tiles;
+    const int32_t* blocks;
+    const int32_t* cells;
+    __device__ __forceinline__ explicit CallView(const uint8_t* call)
+        : h(reinterpret_cast<const CallHeader*>(call)),
+          fds(reinterpret_cast<const FrameDesc*>(call + h->off_fds)),
+          maps0(reinterpret_cast<const CUtensorMap*>(call + h->off_maps0)),
+          mapsk(reinterpret_cast<const CUtensorMap*>(call + h->off_mapsk)),
+          tiles(reinterpret_cast<const int32_t*>(call + h->off_tiles)),
+          blocks(reinterpret_cast<const int32_t*>(call + h->off_blocks)),
+          cells(reinterpret_cast<const int32_t*>(call + h->off_cells)) {}
 };
 
-// ---------------------------------------------------------------------------
-// Pyramid: one thread owns a B x B block of level 0 (B = 2^(L-1)) and writes
-// every level-k pixel that block produces, k = 1..L-1.  Level k+1 is the 2x2
-// mean of level k rounded half up, taken from the rounded level-k values.
-// ---------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(256) pyramid_kernel(const CallHeader* __restrict__ hdr,
-                                                      const FrameDesc* __restrict__ fds,
-                                                      const int32_t* __restrict__ block_start) {
-    constexpr int B = 1 << (L - 1);
-    const int nf = hdr->n_frames;
-    // frame owning this block: block_start is the prefix sum of blocks per frame
-    int lo = 0, hi = nf - 1;
-    const int b = blockIdx.x;
+// Largest i in [0, n) with a[i] <= v, for a non-decreasing a with a[0] <= v.
+__device__ __forceinline__ int upper_index(const int32_t* a, int n, int v) {
+    int lo = 0, hi = n - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (block_start[mid] <= b) lo = mid; else hi = mid - 1;
+        const int mid = (lo + hi + 1) >> 1;
+        if (a[mid] <= v) lo = mid; else hi = mid - 1;
     }
-    const FrameDesc& fd = fds[lo];
-    const int lb = b - block_start[lo];
-    const int tx = (lb % fd.pyr_bx) * 32 + (threadIdx.x & 31);
-    const int ty = (lb / fd.pyr_bx) * 8 + (threadIdx.x >> 5);
+    return lo;
+}
 
-    // level-1 values of this block, computed from level 0
+// ---------------------------------------------------------------------------
+// Pyramid: one thread owns 16 columns x B rows of level 0 (B = 2^(L-1)) and
+// writes every pixel of levels 1..L-1 that block produces.  Level k+1 is the
+// 2x2 mean of level k rounded half up, (a+b+c+d+2)>>2, taken from the
+// rounded level-k values.  Level 0 is read with 16-byte loads; level 1 is
+// computed two pixels per 32-bit word (16-bit lanes) and stored 8 bytes at a
+// time; the coarser levels, a quarter of the work each, are scalar.
+// A CTA covers 512 columns x 8B rows; the grid strides over all CTAs of all
+// frames (blocks[] is the per-frame prefix sum).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pair_sums(uint32_t w) {  // [w0+w1, w2+w3] in 16-bit lanes
+    return (w & 0x00FF00FFu) + ((w >> 8) & 0x00FF00FFu);
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) pyramid_kernel(const uint8_t* __restrict__ call) {
+    constexpr int B = 1 << (L - 1);
     constexpr int B1 = B / 2;
-    uint32_t v[B1][B1];
-    const int W = fd.w, H = fd.h;
-    const int W1 = W >> 1, H1 = H >> 1;
-    const uint8_t* src = fd.lev[0];
-    const int sp = fd.pitch[0];
+    const CallView cv(call);
+    const int nf = cv.h->n_frames, nb = cv.h->n_pyr_blocks;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int f = upper_index(cv.blocks, nf, b);
+        const FrameDesc& fd = cv.fds[f];
+        const int lb = b - cv.blocks[f];
+        const int tx = (lb % fd.pyr_bx) * 32 + (threadIdx.x & 31);
+        const int ty = (lb / fd.pyr_bx) * 8 + (threadIdx.x >> 5);
+        const int W = fd.w, H = fd.h;
+        const int x0 = tx * 16, y0 = ty * B;
+        if (x0 >= W || y0 >= H) continue;
+        const int W1 = W >> 1, H1 = H >> 1;
+        const uint8_t* src = fd.lev[0];
+        const int sp = fd.pitch[0];
+        // level 0 rows; the last partial chunk of a row is read byte by byte
+        uint4 r[B];
 #pragma unroll
-    for (int j = 0; j < B1; ++j) {
-        const int y1 = ty * B1 + j;
-#pragma unroll
-        for (int i = 0; i < B1; ++i) {
-            const int x1 = tx * B1 + i;
-            uint32_t s = 0;
-            if (x1 < W1 && y1 < H1) {
-                const uint8_t* p = src + (size_t)(2 * y1) * sp + 2 * x1;
-                s = (p[0] + p[1] + p[sp] + p[sp + 1] + 2u) >> 2;
-                fd.lev[1][(size_t)y1 * fd.pitch[1] + x1] = (uint8_t)s;
+        for (int j = 0; j < B; ++j) {
+            const int y = y0 + j;
+            r[j] = make_uint4(0, 0, 0, 0);
+            if (y < H) {
+                const uint8_t* p = src + (size_t)y * sp + x0;
+                if (x0 + 16 <= W) {
+                    r[j] = *reinterpret_cast<const uint4*>(p);
+                } else {
+                    uint32_t wv[4] = {0, 0, 0, 0};
+                    for (int i = 0; i < W - x0; ++i) wv[i >> 2] |= (uint32_t)p[i] << (8 * (i & 3));
+                    r[j] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                }
             }
-            v[j][i] = s;
         }
-    }
-    // higher levels from the registers
-    int Wk = W1, Hk = H1;
-#pragma unroll
-    for (int k = 2; k < L; ++k) {
-        const int n = B >> k;       // pixels of level k per thread per axis
-        Wk >>= 1;
-        Hk >>= 1;
-        uint8_t* dst = fd.lev[k];
-        const int dp = fd.pitch[k];
+        // level 1: 8 pixels per row as 4 words of two 16-bit lanes
+        uint32_t q[B1][4];
 #pragma unroll
         for (int j = 0; j < B1; ++j) {
+            const uint32_t t[4] = {r[2 * j].x, r[2 * j].y, r[2 * j].z, r[2 * j].w};
+            const uint32_t u[4] = {r[2 * j + 1].x, r[2 * j + 1].y, r[2 * j + 1].z, r[2 * j + 1].w};
 #pragma unroll
-            for (int i = 0; i < B1; ++i) {
-                if (j < n && i < n) {
-                    const uint32_t s = (v[2 * j][2 * i] + v[2 * j][2 * i + 1] + v[2 * j + 1][2 * i] +
-                                        v[2 * j + 1][2 * i + 1] + 2u) >> 2;
-                    const int xk = tx * n + i, yk = ty * n + j;
-                    if (xk < Wk && yk < Hk) dst[(size_t)yk * dp + xk] = (uint8_t)s;
-                    v[j][i] = s;
-                }
+            for (int w = 0; w < 4; ++w)
+                q[j][w] = ((pair_sums(t[w]) + pair_sums(u[w]) + 0x00020002u) >> 2) & 0x00FF00FFu;
+            const int y1 = ty * B1 + j, x1 = tx * 8;
+            if (y1 < H1 && x1 < W1) {
+                // pixels past W1 land in the row padding of the resident level (pitch >= W1 rounded to 128)
+                const uint2 v = make_uint2(__byte_perm(q[j][0], q[j][1], 0x6420), __byte_perm(q[j][2], q[j][3], 0x6420));
+                *reinterpret_cast<uint2*>(fd.lev[1] + (size_t)y1 * fd.pitch[1] + x1) = v;
+            }
+        }
+        if (L > 2) {
+            // level 1 as scalars, then levels 2.. from the rounded values
+            constexpr int N1 = 8;
+            uint32_t v[B1][N1];
+#pragma unroll
+            for (int j = 0; j < B1; ++j)
+#pragma unroll
+                for (int i = 0; i < N1; ++i) v[j][i] = (q[j][i >> 1] >> (16 * (i & 1))) & 0xFFu;
+            int Wk = W1, Hk = H1, rows = B1, cols = N1;
+#pragma unroll
+            for (int k = 2; k < L; ++k) {
+                rows >>= 1;
+                cols >>= 1;
+                Wk >>= 1;
+                Hk >>= 1;
+                uint8_t* dst = fd.lev[k];
+                const int dp = fd.pitch[k];
+#pragma unroll
+                for (int j = 0; j < B1; ++j)
+#pragma unroll
+                    for (int i = 0; i < N1; ++i)
+                        if (j < rows && i < cols) {
+                            const uint32_t sum = v[2 * j][2 * i] + v[2 * j][2 * i + 1] + v[2 * j + 1][2 * i] +
+                                                 v[2 * j + 1][2 * i + 1] + 2u;
+                            v[j][i] = sum >> 2;
+                            const int xk = tx * cols + i, yk = ty * rows + j;
+                            if (xk < Wk && yk < Hk) dst[(size_t)yk * dp + xk] = (uint8_t)v[j][i];
+                        }
             }
         }
     }
@@ -115,13 +177,13 @@ __global__ void __launch_bounds__(256) pyramid_kernel(const CallHeader* __restri
 // ---------------------------------------------------------------------------
 
 // Radius-3 Bresenham circle, clockwise from the top (Section II-D).
-__device__ __forceinline__ int circ_dx(int i) {
-    constexpr int8_t d[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
-    return d[i];
+__host__ __device__ constexpr int circ_dx(int i) {
+    return i == 0 ? 0 : i == 1 ? 1 : i == 2 ? 2 : i <= 5 ? 3 : i == 6 ? 2 : i == 7 ? 1 : i == 8 ? 0
+         : i == 9 ? -1 : i == 10 ? -2 : i <= 13 ? -3 : i == 14 ? -2 : -1;
 }
-__device__ __forceinline__ int circ_dy(int i) {
-    constexpr int8_t d[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
-    return d[i];
+__host__ __device__ constexpr int circ_dy(int i) {
+    return i <= 1 ? -3 : i == 2 ? -2 : i == 3 ? -1 : i == 4 ? 0 : i == 5 ? 1 : i == 6 ? 2 : i <= 9 ? 3
+         : i == 10 ? 2 : i == 11 ? 1 : i == 12 ? 0 : i == 13 ? -1 : i == 14 ? -2 : -3;
 }
 
 // Start positions s (bits 0..15) of cyclic runs of >= n ones in the 16-bit
@@ -129,7 +191,7 @@ __device__ __forceinline__ int circ_dy(int i) {
 // runs of 8 come from three AND-shift doublings and the run of n from two
 // overlapping runs of 8 that are n-8 apart.
 __device__ __forceinline__ uint32_t arc_starts(uint32_t m, int n) {
-    uint32_t r = m | (m << 16);
+    uint32_t r = m * 0x10001u;
     r &= r >> 1;
     r &= r >> 2;
     r &= r >> 4;
@@ -142,48 +204,56 @@ __device__ __forceinline__ uint32_t rotl16(uint32_t m, int s) {
     return ((m << s) | (m >> (16 - s))) & 0xFFFFu;
 }
 
-// Score of the pixel at smem pointer p (row pitch P); 0 if not a corner.
-template <int MODE>
-__device__ __forceinline__ uint32_t fast_score(const uint8_t* __restrict__ p, int P, int t, int n) {
-    const int c = p[0];
-    const int hi = c + t, lo = c - t;
-    // coarse test (CCRF of Algorithm 1): an arc of >= 9 contains two
-    // cyclically adjacent compass points (0,4), (4,8), (8,12) or (12,0).
-    {
-        const int v0 = p[-3 * P], v4 = p[3], v8 = p[3 * P], v12 = p[-3];
-        const bool b0 = v0 > hi, b4 = v4 > hi, b8 = v8 > hi, b12 = v12 > hi;
-        const bool d0 = v0 < lo, d4 = v4 < lo, d8 = v8 < lo, d12 = v12 < lo;
-        const bool pass = ((b0 | b8) & (b4 | b12)) | ((d0 | d8) & (d4 | d12));
-        if (!pass) return 0;
-    }
-    int v[16];
-    uint32_t bm = 0, dm = 0;
+// Four bytes packed into one word, byte 0 first.
+__device__ __forceinline__ uint32_t pack4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    return __byte_perm(__byte_perm(a, b, 0x0040), __byte_perm(c, d, 0x0040), 0x5410);
+}
+
+// Full segment test and score of the pixel at shared-memory pointer p in a
+// tile of row pitch P (compile time).  Returns 0 when it is not a corner.
+//
+// Eq. 1 labels come from one IMAD per circle point: with
+//   W = ((0x7FFF - c - t) | (0x7FFF + c - t) << 16) + v * (1 - 2^16)
+// the low 16-bit lane is v + 0x7FFF - (c + t), whose bit 15 is set exactly
+// when v > c + t (brighter), and the high lane is 0x7FFF + (c - t) - v,
+// whose bit 31 is set exactly when v < c - t (darker).  Neither lane leaves
+// its 16 bits, so the two compares are exact for all v, c in 0..255 and
+// t in 0..255.  Shifting the flags down point by point gives the 16-bit
+// bright mask in bits 0..15 and the dark mask in bits 16..31, bit i = point i.
+template <int MODE, int P>
+__device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, int t, int n) {
+    const uint32_t c = p[0];
+    uint32_t v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * P + circ_dx(i)];
+    const uint32_t K = ((0x7FFFu - c - (uint32_t)t) & 0xFFFFu) | ((0x7FFFu + c - (uint32_t)t) << 16);
+    uint32_t acc = 0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        v[i] = p[circ_dy(i) * P + circ_dx(i)];
-        bm |= (uint32_t)(v[i] > hi) << i;
-        dm |= (uint32_t)(v[i] < lo) << i;
+        const uint32_t w = K + v[i] * 0xFFFF0001u;
+        acc = (acc >> 1) | (w & 0x80008000u);
     }
+    const uint32_t bm = acc & 0xFFFFu, dm = acc >> 16;
     // at most one polarity can hold n >= 9 points
     const bool bright = __popc(bm) >= n;
-    const uint32_t m = bright ? bm : dm;
-    const uint32_t starts = arc_starts(m, n);
+    const uint32_t starts = arc_starts(bright ? bm : dm, n);
     if (starts == 0) return 0;
-    if (MODE == 0) {  // SAD-B
-        uint32_t s = 0;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) s += (uint32_t)abs(v[i] - c);
+    if (MODE == 0) {  // SAD-B: sum of |I_x - I_c| over the circle
+        const uint32_t c4 = c * 0x01010101u;
+        uint32_t s = __vsadu4(pack4(v[0], v[1], v[2], v[3]), c4);
+        s += __vsadu4(pack4(v[4], v[5], v[6], v[7]), c4);
+        s += __vsadu4(pack4(v[8], v[9], v[10], v[11]), c4);
+        s += __vsadu4(pack4(v[12], v[13], v[14], v[15]), c4);
         return s;
     } else if (MODE == 1) {  // SAD-A: the run is the union of all passing windows
-        uint32_t r = starts;
-        uint32_t d = r;
+        uint32_t d = starts;
         d |= rotl16(d, 1);
         d |= rotl16(d, 2);
         d |= rotl16(d, 4);  // windows of 8 starting at each start
         const uint32_t run = d | rotl16(d, n - 8);
         uint32_t s = 0;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) s += ((run >> i) & 1u) ? (uint32_t)abs(v[i] - c) : 0u;
+        for (int i = 0; i < 16; ++i) s += ((run >> i) & 1u) ? (uint32_t)abs((int)v[i] - (int)c) : 0u;
         return s;
     } else {  // MT: largest window minimum of the arc's polarity, minus 1
         // Raising the threshold only removes points from the masks, so only
@@ -191,7 +261,7 @@ __device__ __forceinline__ uint32_t fast_score(const uint8_t* __restrict__ p, in
         // difference d (strictly above the threshold) gives MT = d - 1.
         int dp[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) dp[i] = bright ? v[i] - c : c - v[i];
+        for (int i = 0; i < 16; ++i) dp[i] = bright ? (int)v[i] - (int)c : (int)c - (int)v[i];
         int best = 0;
 #pragma unroll
         for (int s0 = 0; s0 < 16; ++s0) {
@@ -207,136 +277,357 @@ __device__ __forceinline__ uint32_t fast_score(const uint8_t* __restrict__ p, in
     }
 }
 
+// Coarse test (the CCRF of Algorithm 1) for the 4 pixels of one shared-memory
+// word.  An arc of n >= 9 contiguous points contains floor(n/4) >= 2
+// cyclically consecutive compass points (0, 4, 8, 12), all of them darker or
+// brighter and therefore all with |I_x - I_c| > t.  The test keeps a pixel
+// when two adjacent compass points (n <= 11) or three of the four (n >= 12)
+// differ from the centre by more than t, so it never drops a corner.
+//   C, L, R: the word and its left/right neighbours in the centre row;
+//   N, S: the words 3 rows up and down.
+// Returns bit 7 of byte j set for each kept pixel j.  k7 and the branch on
+// t >= 128 implement the byte-wise compare d > t exactly (see below).
+template <bool HIGH_T, bool THREE>
+__device__ __forceinline__ uint32_t coarse4(uint32_t C, uint32_t L, uint32_t R, uint32_t N, uint32_t S,
+                                            uint32_t k7) {
+    const uint32_t E = __byte_perm(C, R, 0x6543);  // pixels x+3 .. x+6
+    const uint32_t W = __byte_perm(L, C, 0x4321);  // pixels x-3 .. x
+    const uint32_t dn = __vabsdiffu4(N, C), ds = __vabsdiffu4(S, C);
+    const uint32_t de = __vabsdiffu4(E, C), dw = __vabsdiffu4(W, C);
+    // Byte-wise d > t without carries between bytes: with k7 = 127 - t
+    // (t < 128), (d & 0x7F) + k7 carries into bit 7 iff (d & 0x7F) > t, and
+    // a set bit 7 of d alone means d >= 128 > t; with k7 = 255 - t
+    // (t >= 128) the carry means (d & 0x7F) > t - 128, which counts only
+    // together with bit 7 of d.
+    constexpr uint32_t M7 = 0x7F7F7F7Fu;
+    uint32_t fn = (dn & M7) + k7, fs = (ds & M7) + k7, fe = (de & M7) + k7, fw = (dw & M7) + k7;
+    if (HIGH_T) {
+        fn &= dn; fs &= ds; fe &= de; fw &= dw;
+    } else {
+        fn |= dn; fs |= ds; fe |= de; fw |= dw;
+    }
+    uint32_t keep;
+    if (THREE)  // at least 3 of 4 (any 3 of 4 cyclic positions are consecutive)
+        keep = (fn & fe & (fs | fw)) | (fs & fw & (fn | fe));
+    else        // two adjacent: (N|S) & (E|W)
+        keep = (fn | fs) & (fe | fw);
+    return keep & 0x80808080u;
+}
+
 // ---------------------------------------------------------------------------
 // Fused detect: persistent CTAs pull (frame, level, tile) items from a
-// counter.  Per item: TMA-load the tile plus a 4-pixel halo (3 for the
-// circle, 1 for NMS), score the tile plus a 1-pixel ring into shared
-// memory, then apply 3x3 NMS and fold survivors into the cell keys.
+// counter.  A tile is 120 x TH level pixels; its "score region" adds a ring
+// (4 px left and right, 1 row up and down) so that it is exactly 128 pixels
+// = 32 words wide and one warp covers one row.  Per item:
+//   1. TMA loads the region plus the 3-pixel circle halo (box 144 x TH+8).
+//   2. Coarse test on every score-region pixel, one 4-pixel word per lane;
+//      a multiply packs each word's 4 keep flags into a nibble in smem.
+//   3. Each warp compacts the nibbles of its rows into its own queue.
+//   4. Each warp runs the full segment test and score on its queue, writes
+//      scores into the score tile and compacts the corners in place.
+//   5. After a block barrier (NMS reads other warps' rows), 3x3 NMS on the
+//      corner lists; the survivors' packed keys are max-reduced per cell
+//      within the warp (match + __reduce_max_sync) and folded into the
+//      global cell key with one atomicMax per cell and warp.
+// The next item's TMA load is issued as soon as step 4 no longer needs the
+// image tile.
 // ---------------------------------------------------------------------------
-template <int TW, int TH>
+template <int TH>
 struct TileGeom {
-    static constexpr int BW = TW + 32;  // box width: x from x0-16, 16-byte aligned
-    static constexpr int BH = TH + 8;   // box height: y from y0-4
+    static constexpr int TW = 120;         // output pixels per tile row
+    static constexpr int SW = 128;         // score-region width (x0-4 .. x0+124)
+    static constexpr int SR = TH + 2;      // score-region rows (y0-1 .. y0+TH+1)
+    static constexpr int BW = 144;         // TMA box width (16-byte multiple)
+    static constexpr int BH = TH + 8;      // box rows y0-4 .. y0+TH+4
     static constexpr int BOX = BW * BH;
-    static constexpr int SW = TW + 2;   // score tile with a 1-pixel ring
-    static constexpr int SH = TH + 2;
+    static constexpr int WARPS = 8;
+    static constexpr int RPW = SR / WARPS; // score rows per warp
+    static constexpr int QCAP = RPW * SW;  // per-warp queue capacity (every pixel)
     static constexpr int IMG_OFF = 0;
     static constexpr int SC_OFF = (BOX + 127) / 128 * 128;
-    static constexpr int SMEM = SC_OFF + SW * SH * 2 + 128;  // +128: base alignment slack
-    static_assert(TW % 16 == 0 && BW <= 256 && BH <= 256, "TMA box limits");
+    static constexpr int NIB_OFF = SC_OFF + SR * SW * 2;
+    static constexpr int Q_OFF = NIB_OFF + SR * 32;
+    static constexpr int SMEM = Q_OFF + WARPS * QCAP * 2 + 128;  // +128: base alignment slack
+    static_assert(SR % WARPS == 0, "score rows must split evenly over the warps");
+    static_assert(BH <= 256, "TMA box limit");
 };
 
-template <int TW, int TH, int MODE>
-__global__ void __launch_bounds__(256) fast_nms_cell_kernel(
-    const CallHeader* __restrict__ hdr, const FrameDesc* __restrict__ fds,
-    const CUtensorMap* __restrict__ maps0, const CUtensorMap* __restrict__ mapsk,
-    const WorkItem* __restrict__ items, int32_t* __restrict__ counter, uint32_t* __restrict__ status) {
-    using G = TileGeom<TW, TH>;
+constexpr int kThreads = 256;
+
+template <bool HIGH_T, bool THREE, int TH>
+__device__ __forceinline__ void coarse_rows(const uint8_t* img, uint8_t* nib, int xw, uint32_t k7, int warp,
+                                            int lane, int row_lo, int row_hi, bool lane_ok) {
+    using G = TileGeom<TH>;
+    constexpr int RW = G::BW / 4;
+#pragma unroll 2
+    for (int r = warp; r < G::SR; r += G::WARPS) {
+        uint32_t keep = 0;
+        if (r >= row_lo && r < row_hi) {  // uniform per warp
+            const uint32_t* row = reinterpret_cast<const uint32_t*>(img + (3 + r) * G::BW) + xw + lane;
+            keep = coarse4<HIGH_T, THREE>(row[0], row[-1], row[1], row[-3 * RW], row[3 * RW], k7);
+            keep = lane_ok ? keep : 0u;
+        }
+        // bits 7, 15, 23, 31 -> bits 28..31: the product's other terms stay below bit 28
+        nib[r * 32 + lane] = (uint8_t)((keep * 0x00204081u) >> 28);
+    }
+}
+
+// A work item decoded from its index: item i of the call's tile table.
+struct Item {
+    int frame, level, tx, ty;
+};
+
+template <int TH>
+__device__ __forceinline__ Item decode_item(const CallView& cv, int it) {
+    const int n = cv.h->n_frames, L = cv.h->levels;
+    const int j = upper_index(cv.tiles, n * L, it);
+    Item r;
+    r.frame = j % n;
+    r.level = L - 1 - j / n;
+    const int t = it - cv.tiles[j];
+    const int wk = cv.fds[r.frame].w >> r.level;
+    const int ntx = (wk + TileGeom<TH>::TW - 1) / TileGeom<TH>::TW;
+    r.ty = t / ntx;
+    r.tx = t - r.ty * ntx;
+    return r;
+}
+
+template <int TH, int MODE>
+__global__ void __launch_bounds__(kThreads) fast_nms_cell_kernel(const uint8_t* __restrict__ call,
+                                                                 int32_t* __restrict__ counter,
+                                                                 uint32_t* __restrict__ status) {
+    using G = TileGeom<TH>;
     extern __shared__ __align__(128) uint8_t smem_raw[];
     __shared__ uint64_t bar;
     __shared__ int32_t item_sh;
+    __shared__ Item cur_sh;
     // TMA destinations must be 128-byte aligned
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint8_t* img = smem + G::IMG_OFF;
     uint16_t* sc = reinterpret_cast<uint16_t*>(smem + G::SC_OFF);
+    uint8_t* nib = smem + G::NIB_OFF;
 
-    const int tid = threadIdx.x;
+    const CallView cv(call);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint16_t* queue = reinterpret_cast<uint16_t*>(smem + G::Q_OFF) + warp * G::QCAP;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_barrier_init();
     }
+    // the score tile starts zero; only corners are written, and reset after use
+    for (int i = tid; i < G::SR * G::SW / 8; i += kThreads) reinterpret_cast<uint4*>(sc)[i] = make_uint4(0, 0, 0, 0);
+    const int n_items = cv.h->n_items;
+    const int thresh = cv.h->thresh, n_arc = cv.h->arc;
+    const bool high_t = thresh >= 128;
+    const bool three = n_arc >= 12;
+    const uint32_t k7 = (uint32_t)((high_t ? 255 : 127) - thresh) * 0x01010101u;
+
+    // thread 0: takes the next item, publishes it and issues its TMA load
+    auto next_item = [&]() {
+        const int it = atomicAdd(counter, 1);
+        item_sh = it;
+        if (it < n_items) {
+            const Item wi = decode_item<TH>(cv, it);
+            cur_sh = wi;
+            const int x0 = wi.tx * G::TW, y0 = wi.ty * TH;
+            const CUtensorMap* map =
+                wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
+            fence_tensormap_acquire(map);
+            mbar_arrive_expect_tx(&bar, G::BOX);
+            tma_load_2d(img, map, &bar, (x0 - 8) & ~15, y0 - 4);
+        }
+    };
+    // the decode kernel adds up the per-frame counts from zero
+    if (blockIdx.x == 0 && cv.h->counts)
+        for (int f = tid; f < cv.h->n_frames; f += kThreads) cv.h->counts[f] = 0;
+    if (tid == 0) next_item();
     __syncthreads();
-    const int n_items = hdr->n_items;
-    const int thresh = hdr->thresh, n_arc = hdr->arc, cell = hdr->cell;
     uint32_t phase = 0;
 
     for (;;) {
-        if (tid == 0) item_sh = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = item_sh;
-        if (it >= n_items) break;
-        const WorkItem wi = items[it];
-        const FrameDesc& fd = fds[wi.frame];
+        if (item_sh >= n_items) break;
+        const Item wi = cur_sh;
+        const FrameDesc& fd = cv.fds[wi.frame];
         const int k = wi.level;
         const int Wk = fd.w >> k, Hk = fd.h >> k;
-        const int x0 = wi.tx * TW, y0 = wi.ty * TH;
-        if (tid == 0) {
-            const CUtensorMap* map = k == 0 ? &maps0[wi.frame] : &mapsk[wi.frame * (kMaxLevels - 1) + k - 1];
-            fence_tensormap_acquire(map);
-            mbar_arrive_expect_tx(&bar, G::BOX);
-            tma_load_2d(img, map, &bar, x0 - 16, y0 - 4);
-        }
+        const int x0 = wi.tx * G::TW, y0 = wi.ty * TH;
+        const uint32_t magic = cv.h->cell_magic[k];
+        // score column 0 is level x = x0 - 4; box column 0 is ((x0 - 8) & ~15)
+        const int xoff = x0 - 4 - ((x0 - 8) & ~15);  // 4 or 12
         const bool ok = mbar_wait_bounded(&bar, phase, kWaitLimitNs);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) {
             if (tid == 0) atomicOr(status, kStatusTimeout);
             return;
         }
-        // scores of the tile plus a 1-pixel ring
-        for (int i = tid; i < G::SW * G::SH; i += blockDim.x) {
-            const int sy = i / G::SW, sx = i - sy * G::SW;
-            const int x = x0 - 1 + sx, y = y0 - 1 + sy;
+
+        // 2. coarse test -> nibbles.  Rows/columns with no testable pixel
+        // (outside 3 <= x < Wk-3, 3 <= y < Hk-3) are skipped.
+        {
+            const int row_lo = max(0, 4 - y0), row_hi = min(G::SR, Hk - 2 - y0);
+            const int lx = x0 - 4 + 4 * lane;
+            const bool lane_ok = lx + 3 >= 3 && lx < Wk - 3;
+            if (high_t) {
+                if (three) coarse_rows<true, true, TH>(img, nib, xoff / 4, k7, warp, lane, row_lo, row_hi, lane_ok);
+                else coarse_rows<true, false, TH>(img, nib, xoff / 4, k7, warp, lane, row_lo, row_hi, lane_ok);
+            } else {
+                if (three) coarse_rows<false, true, TH>(img, nib, xoff / 4, k7, warp, lane, row_lo, row_hi, lane_ok);
+                else coarse_rows<false, false, TH>(img, nib, xoff / 4, k7, warp, lane, row_lo, row_hi, lane_ok);
+            }
+        }
+        __syncwarp();
+
+        // 3. warp-local compaction of this warp's rows (r = warp + 8 j):
+        // nibble word q holds row warp + 8 (q >> 3), pixels 16 (q & 7) .. +15
+        constexpr int WPL = G::RPW * 8 / 32;  // nibble words per lane
+        uint32_t words[WPL > 0 ? WPL : 1];
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < WPL; ++j) {
+            const int q = lane + 32 * j;
+            words[j] = reinterpret_cast<const uint32_t*>(nib + (warp + 8 * (q >> 3)) * 32)[q & 7];
+            cnt += __popc(words[j]);
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        int pos = incl - cnt;
+#pragma unroll
+        for (int j = 0; j < WPL; ++j) {
+            uint32_t m = words[j];
+            const int q = lane + 32 * j;
+            const int base_idx = (warp + 8 * (q >> 3)) * G::SW + 16 * (q & 7);
+            while (m) {
+                const int b = __ffs(m) - 1;  // byte b >> 3, pixel b & 3 of that byte's word
+                m &= m - 1;
+                queue[pos++] = (uint16_t)(base_idx + 4 * (b >> 3) + (b & 7));
+            }
+        }
+        __syncwarp();
+
+        // 4. full test on this warp's queue; corners are compacted in place
+        int ncorner = 0;
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = e0 + lane;
             uint32_t s = 0;
-            if (x >= 3 && y >= 3 && x < Wk - 3 && y < Hk - 3)
-                s = fast_score<MODE>(img + (sy + 3) * G::BW + (sx + 15), G::BW, thresh, n_arc);
-            sc[i] = (uint16_t)s;
+            int idx = 0;
+            if (e < total) {
+                idx = queue[e];
+                const int sr = idx >> 7, scx = idx & 127;
+                const int x = x0 - 4 + scx, y = y0 - 1 + sr;
+                if (x >= 3 && y >= 3 && x < Wk - 3 && y < Hk - 3)
+                    s = eval_corner<MODE, G::BW>(img + (3 + sr) * G::BW + xoff + scx, thresh, n_arc);
+            }
+            const uint32_t cm = __ballot_sync(0xFFFFFFFFu, s != 0);
+            if (s) {
+                sc[idx] = (uint16_t)s;
+                queue[ncorner + __popc(cm & lt_mask)] = (uint16_t)idx;
+            }
+            ncorner += __popc(cm);
         }
-        __syncthreads();
-        // 3x3 NMS and cell maximum
-        for (int i = tid; i < TW * TH; i += blockDim.x) {
-            const int oy = i / TW, ox = i - oy * TW;
-            const uint16_t* q = sc + (oy + 1) * G::SW + (ox + 1);
-            const uint32_t s = q[0];
-            if (s == 0) continue;
-            const bool keep = s >= q[-G::SW - 1] && s >= q[-G::SW] && s >= q[-G::SW + 1] && s >= q[-1] &&
-                              s >= q[1] && s >= q[G::SW - 1] && s >= q[G::SW] && s >= q[G::SW + 1];
-            if (!keep) continue;
-            const int x = x0 + ox, y = y0 + oy;
-            const uint32_t lin = ((uint32_t)k << 28) | (uint32_t)(y * Wk + x);
-            const uint64_t key = ((uint64_t)s << 32) | (uint64_t)(0xFFFFFFFFu - lin);
-            const int cx = (x << k) / cell, cy = (y << k) / cell;
-            atomicMax(reinterpret_cast<unsigned long long*>(&fd.keys[cy * fd.gw + cx]),
-                      (unsigned long long)key);
+        __syncthreads();  // all scores written; the image tile is free
+
+        // prefetch the next item into the image tile
+        if (tid == 0) next_item();
+
+        // 5. NMS on the corners, per-cell warp reduction, atomicMax
+        for (int e0 = 0; e0 < ncorner; e0 += 32) {
+            const int e = e0 + lane;
+            uint32_t cell_id = 0xFFFFFFFFu;
+            uint32_t hi = 0, lo = 0;
+            if (e < ncorner) {
+                const int idx = queue[e];
+                const int sr = idx >> 7, scx = idx & 127;
+                const bool inside = scx >= 4 && scx < 4 + G::TW && sr >= 1 && sr <= TH;
+                if (inside) {
+                    const uint16_t* q = sc + idx;
+                    const uint32_t s = q[0];
+                    const bool keep = s >= q[-G::SW - 1] && s >= q[-G::SW] && s >= q[-G::SW + 1] && s >= q[-1] &&
+                                      s >= q[1] && s >= q[G::SW - 1] && s >= q[G::SW] && s >= q[G::SW + 1];
+                    if (keep) {
+                        const uint32_t x = (uint32_t)(x0 - 4 + scx), y = (uint32_t)(y0 - 1 + sr);
+                        cell_id = __umulhi(y, magic) * (uint32_t)fd.gw + __umulhi(x, magic);
+                        hi = s;
+                        lo = 0xFFFFFFFFu - (((uint32_t)k << 28) | (y * (uint32_t)Wk + x));
+                    }
+                }
+            }
+            // one max-reduction of the packed keys per distinct cell, led by
+            // its lowest lane, then one atomicMax per cell
+            uint32_t pend = __ballot_sync(0xFFFFFFFFu, hi != 0);
+            while (pend) {
+                const int leader = __ffs(pend) - 1;
+                const uint32_t c = __shfl_sync(0xFFFFFFFFu, cell_id, leader);
+                const uint32_t grp = __ballot_sync(0xFFFFFFFFu, hi != 0 && cell_id == c);
+                if ((grp >> lane) & 1u) {
+                    const uint32_t hmax = __reduce_max_sync(grp, hi);
+                    const uint32_t lmax = __reduce_max_sync(grp, hi == hmax ? lo : 0u);
+                    if (lane == leader)
+                        atomicMax(reinterpret_cast<unsigned long long*>(&fd.keys[c]),
+                                  ((unsigned long long)hmax << 32) | lmax);
+                }
+                pend &= ~grp;
+            }
         }
-        __syncthreads();
+        __syncthreads();  // every warp's NMS has read its neighbours
+        for (int e = lane; e < ncorner; e += 32) sc[queue[e]] = 0;
+        // the next iteration's barrier (after its TMA wait) orders these
+        // resets before any score write of the next item
     }
 }
 
 // ---------------------------------------------------------------------------
-// Decode: one CTA per frame turns keys into records, counts non-empty cells
-// and clears the keys (and the work counter) for the next call.
+// Decode: one thread per cell of all frames turns its key into a record,
+// clears the key for the next call and counts non-empty cells per frame
+// (warp-aggregated; the fused kernel zeroed the counts).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) decode_kernel(const CallHeader* __restrict__ hdr,
-                                                     const FrameDesc* __restrict__ fds,
-                                                     int32_t* __restrict__ counter) {
-    const FrameDesc& fd = fds[blockIdx.x];
-    const int ncell = fd.gw * fd.gh;
-    int cnt = 0;
-    for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
-        const uint64_t key = fd.keys[i];
-        int4 rec = make_int4(-1, -1, -1, 0);
-        if (key != 0) {
-            const uint32_t lin = 0xFFFFFFFFu - (uint32_t)key;
-            const int k = (int)(lin >> 28);
-            const uint32_t idx = lin & 0x0FFFFFFFu;
-            const uint32_t wk = (uint32_t)(fd.w >> k);
-            const int y = (int)(idx / wk), x = (int)(idx - (uint32_t)y * wk);
-            rec = make_int4(x << k, y << k, k, (int)(key >> 32));
-            fd.keys[i] = 0;
-            ++cnt;
+__global__ void __launch_bounds__(256) decode_kernel(const uint8_t* __restrict__ call, int32_t* __restrict__ counter) {
+    const CallView cv(call);
+    const int nf = cv.h->n_frames, total = cv.h->n_cells;
+    int32_t* counts = cv.h->counts;
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        int f = -1;
+        bool hit = false;
+        if (i < total) {
+            f = upper_index(cv.cells, nf, i);
+            const FrameDesc& fd = cv.fds[f];
+            const int c = i - cv.cells[f];
+            const uint64_t key = fd.keys[c];
+            int4 rec = make_int4(-1, -1, -1, 0);
+            if (key != 0) {
+                const uint32_t lin = 0xFFFFFFFFu - (uint32_t)key;
+                const int k = (int)(lin >> 28);
+                const uint32_t idx = lin & 0x0FFFFFFFu;
+                const uint32_t wk = (uint32_t)(fd.w >> k);
+                const int y = (int)(idx / wk), x = (int)(idx - (uint32_t)y * wk);
+                rec = make_int4(x << k, y << k, k, (int)(key >> 32));
+                fd.keys[c] = 0;
+                hit = true;
+            }
+            fd.out[c] = rec;
         }
-        fd.out[i] = rec;
+        if (counts) {
+            // lanes of one frame add their hits with one atomic
+            uint32_t pend = __ballot_sync(0xFFFFFFFFu, f >= 0);
+            while (pend) {
+                const int leader = __ffs(pend) - 1;
+                const int fl = __shfl_sync(0xFFFFFFFFu, f, leader);
+                const uint32_t grp = __ballot_sync(0xFFFFFFFFu, f == fl);
+                const uint32_t hits = __popc(__ballot_sync(0xFFFFFFFFu, f == fl && hit));
+                if (lane == leader && hits) atomicAdd(&counts[fl], (int)hits);
+                pend &= ~grp;
+            }
+        }
     }
-    cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-    __shared__ int part[8];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-        if (hdr->counts) hdr->counts[blockIdx.x] = t;
-        if (blockIdx.x == 0) *counter = 0;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
 }
 
 }  // namespace vio

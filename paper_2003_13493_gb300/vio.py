@@ -38,6 +38,20 @@ class Dims(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("pitch", ctypes.c_int32)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("thresh", ctypes.c_int), ("arc_len", ctypes.c_int), ("cell_size", ctypes.c_int),
+                ("levels", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_wait_us", ctypes.c_int),
+                ("lanes", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
+                ("queue_capacity", ctypes.c_int), ("keep_results", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("frames_per_s", ctypes.c_double)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
                 ("cta_per_sm", ctypes.c_int), ("variant", ctypes.c_int)]
@@ -97,6 +111,22 @@ def load(build_if_missing: bool = True):
     lib.vio_get_tuning.restype = st
     lib.vio_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
     lib.vio_set_tuning.restype = st
+    lib.vio_device.argtypes = [P]
+    lib.vio_device.restype = ci
+    lib.vio_serve_config_default.argtypes = [ctypes.POINTER(ServeConfig)]
+    lib.vio_serve_config_default.restype = None
+    lib.vio_serve_start.argtypes = [P, ctypes.POINTER(ServeConfig)]
+    lib.vio_serve_start.restype = st
+    lib.vio_submit.argtypes = [P, ci, P, Dims, ctypes.POINTER(ctypes.c_uint64)]
+    lib.vio_submit.restype = st
+    lib.vio_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ci)]
+    lib.vio_poll.restype = st
+    lib.vio_serve_drain.argtypes = [P, ci]
+    lib.vio_serve_drain.restype = st
+    lib.vio_serve_stats.argtypes = [P, ctypes.POINTER(ServeStats)]
+    lib.vio_serve_stats.restype = st
+    lib.vio_serve_stop.argtypes = [P]
+    lib.vio_serve_stop.restype = st
     lib.vio_num_variants.argtypes = []
     lib.vio_num_variants.restype = ci
     lib.vio_variant.argtypes = [ci, ctypes.POINTER(Tuning)]
@@ -223,6 +253,57 @@ class Detector:
 
     def sync(self, stream=None):
         self._check(self.lib.vio_sync(self.ctx, _stream_handle(stream)))
+
+    # ---- serving -------------------------------------------------------------
+    def serve_start(self, **kw):
+        """Starts the context's scheduler; keyword arguments override the
+        fields of vio_serve_config (thresh, arc_len, cell_size, levels,
+        max_batch, max_wait_us, lanes, mem_budget_bytes, queue_capacity,
+        keep_results)."""
+        cfg = ServeConfig()
+        self.lib.vio_serve_config_default(ctypes.byref(cfg))
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        self.serve_cfg = cfg
+        self._check(self.lib.vio_serve_start(self.ctx, ctypes.byref(cfg)))
+
+    def submit(self, stream_id: int, frame: np.ndarray) -> int:
+        """Queues a host frame (kept alive by the caller until it completes)."""
+        if frame.dtype != np.uint8 or frame.ndim != 2 or frame.strides[1] != 1:
+            raise ValueError("frame must be a 2-D uint8 array with unit column stride")
+        t = ctypes.c_uint64()
+        d = Dims(frame.shape[1], frame.shape[0], frame.strides[0])
+        s = self.lib.vio_submit(self.ctx, stream_id, ctypes.c_void_p(frame.ctypes.data), d, ctypes.byref(t))
+        if s != 0:
+            raise VioError(s, self.lib.vio_status_str(s).decode())
+        return t.value
+
+    def submit_raw(self, stream_id: int, ptr: int, dims: Dims) -> tuple[int, int]:
+        """(status, ticket) without raising, for load generators."""
+        t = ctypes.c_uint64()
+        s = self.lib.vio_submit(self.ctx, stream_id, ctypes.c_void_p(ptr), dims, ctypes.byref(t))
+        return s, t.value
+
+    def poll(self, ticket: int, w: int, h: int):
+        """(done, cells (ncells, 4) int32 or None, count)."""
+        cfg = self.serve_cfg
+        out = np.empty((num_cells(w, h, cfg.cell_size), 4), dtype=np.int32)
+        cnt = ctypes.c_int32()
+        done = ctypes.c_int()
+        self._check(self.lib.vio_poll(self.ctx, ticket, ctypes.c_void_p(out.ctypes.data), ctypes.byref(cnt),
+                                      ctypes.byref(done)))
+        return (True, out, cnt.value) if done.value else (False, None, 0)
+
+    def drain(self, timeout_ms: int = 60000):
+        self._check(self.lib.vio_serve_drain(self.ctx, timeout_ms))
+
+    def serve_stats(self) -> dict:
+        st = ServeStats()
+        self._check(self.lib.vio_serve_stats(self.ctx, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServeStats._fields_}
+
+    def serve_stop(self):
+        self._check(self.lib.vio_serve_stop(self.ctx))
 
     def set_variant(self, variant: int | None):
         if variant is None:

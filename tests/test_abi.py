@@ -46,7 +46,9 @@ def test_variants_listed(lib):
     vs = vio.variants()
     assert len(vs) >= 3
     for tw, th in vs:
-        assert tw % 16 == 0 and tw + 32 <= 256 and th + 8 <= 256
+        # a score region of tw + 8 = 128 pixels (one warp of 4-pixel words per
+        # row) and th + 2 rows split over 8 warps in groups of 4
+        assert tw + 8 == 128 and (th + 2) % 32 == 0 and th + 8 <= 256
     t = vio.Tuning()
     assert lib.vio_variant(len(vs), ctypes.byref(t)) == 1
 
