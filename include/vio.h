@@ -245,6 +245,44 @@ vio_status vio_serve_stats(vio_ctx* ctx, vio_serve_stats_t* out);
 /* Finishes the queued frames, stops the scheduler, frees the lanes. */
 vio_status vio_serve_stop(vio_ctx* ctx);
 
+/*
+ * Detection of one frame that allocates nothing.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate when
+ * they need a detection: code running under a memory pool that accounts for
+ * every byte, real-time loops that may not pay cudaMalloc's device-wide
+ * synchronisation and unbounded latency, or plug-ins whose host process owns
+ * all allocations.  No context is used.  The working memory besides the
+ * caller's frame and outputs (call block, counters, cell keys, pyramid
+ * levels) is one fixed array of VIO_NOALLOC_SCRATCH_BYTES that the library
+ * keeps on every device that loads it, until the process exits.
+ *
+ *   frame      DEVICE pointer, 16-byte aligned, dims.pitch a multiple of 16
+ *   dims       as vio_detect; the frame must fit the array:
+ *              4096 + 8 * cells (rounded up to 256)
+ *              + sum over k >= 1 of round_up(w >> k, 128) * (h >> k),
+ *              each level rounded up to 256, must not exceed
+ *              VIO_NOALLOC_SCRATCH_BYTES (frames up to 3840 x 2160 at 4
+ *              levels fit); larger frames return VIO_ERR_INVALID_ARG
+ *              before anything is enqueued
+ *   thresh, arc_len, cell_size, levels   as vio_detect
+ *   score      a vio_score
+ *   out_cells  DEVICE, vio_num_cells(w, h, cell_size) records
+ *   out_count  DEVICE int32 receiving the non-empty cell count, or NULL
+ *
+ * Asynchronous on `stream`; the results equal vio_detect's.  Every call
+ * shares the one array and clears the parts that must start at zero, so
+ * calls that overlap on the GPU (another stream, another host thread) race
+ * and must be serialised by the caller.  The first call on each device sets
+ * up that device (it looks up the array's device address, with the device
+ * current); make that first call before any stream capture.  A bounded
+ * device-side wait that expires is not reported here (use vio_detect and
+ * vio_sync where that matters).  Errors: VIO_ERR_INVALID_ARG,
+ * VIO_ERR_UNSUPPORTED (not an sm_103 device), VIO_ERR_CUDA.
+ */
+#define VIO_NOALLOC_SCRATCH_BYTES (4u << 20)
+vio_status vio_detect_noalloc(const uint8_t* frame, vio_dims dims, int thresh, int arc_len, int cell_size,
+                              int levels, int score, vio_feature* out_cells, int32_t* out_count, vio_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -127,6 +127,8 @@ def load(build_if_missing: bool = True):
     lib.vio_serve_stats.restype = st
     lib.vio_serve_stop.argtypes = [P]
     lib.vio_serve_stop.restype = st
+    lib.vio_detect_noalloc.argtypes = [P, Dims, ci, ci, ci, ci, ci, P, P, P]
+    lib.vio_detect_noalloc.restype = st
     lib.vio_num_variants.argtypes = []
     lib.vio_num_variants.restype = ci
     lib.vio_variant.argtypes = [ci, ctypes.POINTER(Tuning)]
