@@ -273,10 +273,10 @@ vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s
     if (!ctx->grid_fused[variant]) {
         int occ = 0;
         VIO_CK(cudaFuncSetAttribute(v.fn[mode], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
-        VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn[mode], 256, v.smem));
+        VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn[mode], kThreads, v.smem));
         ctx->grid_fused[variant] = std::max(1, occ) * ctx->sm_count;
     }
-    v.fn[mode]<<<ctx->grid_fused[variant], 256, v.smem, s>>>(ctx->d_call, ctx->d_counter, ctx->d_status);
+    v.fn[mode]<<<ctx->grid_fused[variant], kThreads, v.smem, s>>>(ctx->d_call, ctx->d_counter, ctx->d_status);
     VIO_CK(cudaGetLastError());
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[2], s, rec_flags));
     decode_kernel<<<ctx->sm_count * 4, 256, 0, s>>>(ctx->d_call, ctx->d_counter);

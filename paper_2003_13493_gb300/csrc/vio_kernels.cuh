@@ -220,7 +220,7 @@ __device__ __forceinline__ uint32_t pack4(uint32_t a, uint32_t b, uint32_t c, ui
 // its 16 bits, so the two compares are exact for all v, c in 0..255 and
 // t in 0..255.  Shifting the flags down point by point gives the 16-bit
 // bright mask in bits 0..15 and the dark mask in bits 16..31, bit i = point i.
-template <int MODE, int P>
+template <int MODE, int P, bool SCORE = true>
 __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, int t, int n) {
     const uint32_t c = p[0];
     uint32_t v[16];
@@ -238,6 +238,7 @@ __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, i
     const bool bright = __popc(bm) >= n;
     const uint32_t starts = arc_starts(bright ? bm : dm, n);
     if (starts == 0) return 0;
+    if (!SCORE) return 1;
     if (MODE == 0) {  // SAD-B: sum of |I_x - I_c| over the circle
         const uint32_t c4 = c * 0x01010101u;
         uint32_t s = __vsadu4(pack4(v[0], v[1], v[2], v[3]), c4);
@@ -275,6 +276,20 @@ __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, i
         }
         return (uint32_t)(best - 1);
     }
+}
+
+// SAD-B of the pixel at p (row pitch P): sum of |I_x - I_c| over the circle.
+template <int P>
+__device__ __forceinline__ uint32_t sad_b(const uint8_t* __restrict__ p) {
+    const uint32_t c4 = p[0] * 0x01010101u;
+    uint32_t v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * P + circ_dx(i)];
+    uint32_t s = __vsadu4(pack4(v[0], v[1], v[2], v[3]), c4);
+    s += __vsadu4(pack4(v[4], v[5], v[6], v[7]), c4);
+    s += __vsadu4(pack4(v[8], v[9], v[10], v[11]), c4);
+    s += __vsadu4(pack4(v[12], v[13], v[14], v[15]), c4);
+    return s;
 }
 
 // Coarse test (the CCRF of Algorithm 1) for the 4 pixels of one shared-memory
@@ -318,19 +333,21 @@ __device__ __forceinline__ uint32_t coarse4(uint32_t C, uint32_t L, uint32_t R, 
 // Fused detect: persistent CTAs pull (frame, level, tile) items from a
 // counter.  A tile is 120 x TH level pixels; its "score region" adds a ring
 // (4 px left and right, 1 row up and down) so that it is exactly 128 pixels
-// = 32 words wide and one warp covers one row.  Per item:
-//   1. TMA loads the region plus the 3-pixel circle halo (box 144 x TH+8).
-//   2. Coarse test on every score-region pixel, one 4-pixel word per lane;
-//      a multiply packs each word's 4 keep flags into a nibble in smem.
-//   3. Each warp compacts the nibbles of its rows into its own queue.
-//   4. Each warp runs the full segment test and score on its queue, writes
+// wide: 16 lanes of 8 pixels cover a row, a warp covers a pair of rows.
+// Per item:
+//   1. TMA loads the region plus the 3-pixel circle halo (box 144 x TH+8)
+//      into one of two image buffers; the other buffer is loading the next
+//      item meanwhile.
+//   2. Coarse test on every score-region pixel, 8 pixels per lane, pixels
+//      outside the testable area masked off; each warp appends the kept
+//      pixels of each of its row pairs to its own queue (warp scan).
+//   3. Each warp runs the full segment test and score on its queue, writes
 //      scores into the score tile and compacts the corners in place.
-//   5. After a block barrier (NMS reads other warps' rows), 3x3 NMS on the
-//      corner lists; the survivors' packed keys are max-reduced per cell
-//      within the warp (match + __reduce_max_sync) and folded into the
-//      global cell key with one atomicMax per cell and warp.
-// The next item's TMA load is issued as soon as step 4 no longer needs the
-// image tile.
+//   4. After a barrier of the consumer warps (NMS reads other warps' rows),
+//      3x3 NMS on the corner lists; when a warp's survivors share one cell
+//      their packed keys are max-reduced with __reduce_max_sync and folded
+//      into the global cell key with one atomicMax, otherwise each survivor
+//      does its own atomicMax.
 // ---------------------------------------------------------------------------
 template <int TH>
 struct TileGeom {
@@ -340,41 +357,34 @@ struct TileGeom {
     static constexpr int BW = 144;         // TMA box width (16-byte multiple)
     static constexpr int BH = TH + 8;      // box rows y0-4 .. y0+TH+4
     static constexpr int BOX = BW * BH;
+    static constexpr int BOXA = (BOX + 127) / 128 * 128;
     static constexpr int WARPS = 8;
-    static constexpr int RPW = SR / WARPS; // score rows per warp
-    static constexpr int QCAP = RPW * SW;  // per-warp queue capacity (every pixel)
+    static constexpr int PPW = SR / 2 / WARPS;  // row pairs per warp
+    static constexpr int QCAP = PPW * 2 * SW;   // per-warp queue capacity (every pixel)
+    static constexpr int NBUF = 2;              // image buffers in the TMA ring
     static constexpr int IMG_OFF = 0;
-    static constexpr int SC_OFF = (BOX + 127) / 128 * 128;
-    static constexpr int NIB_OFF = SC_OFF + SR * SW * 2;
-    static constexpr int Q_OFF = NIB_OFF + SR * 32;
+    static constexpr int SC_OFF = NBUF * BOXA;
+    static constexpr int Q_OFF = SC_OFF + SR * SW * 2;
     static constexpr int SMEM = Q_OFF + WARPS * QCAP * 2 + 128;  // +128: base alignment slack
-    static_assert(SR % WARPS == 0, "score rows must split evenly over the warps");
+    static_assert(SR % (2 * WARPS) == 0, "row pairs must split evenly over the warps");
     static_assert(BH <= 256, "TMA box limit");
 };
 
-constexpr int kThreads = 256;
-
-template <bool HIGH_T, bool THREE, int TH>
-__device__ __forceinline__ void coarse_rows(const uint8_t* img, uint8_t* nib, int xw, uint32_t k7, int warp,
-                                            int lane, int row_lo, int row_hi, bool lane_ok) {
-    using G = TileGeom<TH>;
-    constexpr int RW = G::BW / 4;
-#pragma unroll 2
-    for (int r = warp; r < G::SR; r += G::WARPS) {
-        uint32_t keep = 0;
-        if (r >= row_lo && r < row_hi) {  // uniform per warp
-            const uint32_t* row = reinterpret_cast<const uint32_t*>(img + (3 + r) * G::BW) + xw + lane;
-            keep = coarse4<HIGH_T, THREE>(row[0], row[-1], row[1], row[-3 * RW], row[3 * RW], k7);
-            keep = lane_ok ? keep : 0u;
-        }
-        // bits 7, 15, 23, 31 -> bits 28..31: the product's other terms stay below bit 28
-        nib[r * 32 + lane] = (uint8_t)((keep * 0x00204081u) >> 28);
-    }
-}
+constexpr int kConsumers = 256;             // 8 warps that detect
+constexpr int kThreads = kConsumers + 32;   // + 1 producer warp (items, TMA)
 
 // A work item decoded from its index: item i of the call's tile table.
 struct Item {
     int frame, level, tx, ty;
+};
+
+// What the consumers need of an item, written by the producer next to the
+// image buffer it fills.
+struct ItemInfo {
+    int32_t id;            // item index; >= n_items ends the consumers' loop
+    int32_t level, x0, y0;
+    int32_t wk, hk, gw, pad;
+    uint64_t* keys;
 };
 
 template <int TH>
@@ -392,137 +402,185 @@ __device__ __forceinline__ Item decode_item(const CallView& cv, int it) {
     return r;
 }
 
+// bits 7, 15, 23, 31 -> bits 28..31: the product's other terms stay below bit 28
+__device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x00204081u) >> 28; }
+
+// Coarse test over this warp's rows, appending kept pixels (score-region index
+// row * 128 + column) to the warp's queue; returns the queue length.
+// Warp w owns row pairs PPW*w .. PPW*w + PPW-1 (lanes 0-15 the even row of a
+// pair, 16-31 the odd one, 8 pixels per lane).  The kept-pixel bits of up to 4
+// row pairs gather in one 32-bit word per lane (bit 8i + j = pair i, pixel j),
+// one warp scan of the popcounts places each lane's run in the queue, and
+// each lane writes its pixels by walking its set bits.
+template <bool HIGH_T, bool THREE, int TH>
+__device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* queue, int xw, uint32_t k7,
+                                                  int warp, int lane, int row_lo, int row_hi, uint32_t vm0,
+                                                  uint32_t vm1) {
+    using G = TileGeom<TH>;
+    constexpr int RW = G::BW / 4;
+    constexpr int NW = (G::PPW + 3) / 4;  // mask words per lane
+    const int half = lane >> 4, g = lane & 15;
+    uint32_t m[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) m[w] = 0u;
+#pragma unroll
+    for (int i = 0; i < G::PPW; ++i) {
+        const int p = G::PPW * warp + i;
+        if (2 * p + 1 < row_lo || 2 * p >= row_hi) continue;  // uniform: no testable row
+        const int r = 2 * p + half;
+        if (r >= row_lo && r < row_hi) {
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(img + (3 + r) * G::BW) + xw + 2 * g;
+            const uint32_t L = w[-1], C0 = w[0], C1 = w[1], R = w[2];
+            const uint32_t k0 = coarse4<HIGH_T, THREE>(C0, L, C1, w[-3 * RW], w[3 * RW], k7) & vm0;
+            const uint32_t k1 = coarse4<HIGH_T, THREE>(C1, C0, R, w[1 - 3 * RW], w[1 + 3 * RW], k7) & vm1;
+            m[i >> 2] |= (nibble(k0) | (nibble(k1) << 4)) << (8 * (i & 3));
+        }
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cnt += __popc(m[w]);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int pos = incl - cnt;
+    // pixel of bit b of word w: pair 4w + (b >> 3), column 8g + (b & 7)
+    const int base = (2 * G::PPW * warp + half) * G::SW + 8 * g;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        uint32_t mw = m[w];
+        while (mw) {
+            const int b = 31 - __clz(mw);
+            mw ^= 1u << b;
+            queue[pos++] = (uint16_t)(base + (4 * w + (b >> 3)) * (2 * G::SW) + (b & 7));
+        }
+    }
+    return __shfl_sync(0xFFFFFFFFu, incl, 31);
+}
+
 template <int TH, int MODE>
 __global__ void __launch_bounds__(kThreads) fast_nms_cell_kernel(const uint8_t* __restrict__ call,
                                                                  int32_t* __restrict__ counter,
                                                                  uint32_t* __restrict__ status) {
     using G = TileGeom<TH>;
+    constexpr int NB = G::NBUF;
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    __shared__ uint64_t bar;
-    __shared__ int32_t item_sh;
-    __shared__ Item cur_sh;
+    __shared__ uint64_t full_bar[NB], empty_bar[NB];
+    __shared__ ItemInfo info[NB];
     // TMA destinations must be 128-byte aligned
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint8_t* img = smem + G::IMG_OFF;
     uint16_t* sc = reinterpret_cast<uint16_t*>(smem + G::SC_OFF);
-    uint8_t* nib = smem + G::NIB_OFF;
 
     const CallView cv(call);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint16_t* queue = reinterpret_cast<uint16_t*>(smem + G::Q_OFF) + warp * G::QCAP;
-    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int n_items = cv.h->n_items;
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&full_bar[b], 1);
+            mbar_init(&empty_bar[b], kConsumers / 32);  // one arrival per consumer warp
+        }
         fence_barrier_init();
     }
     // the score tile starts zero; only corners are written, and reset after use
     for (int i = tid; i < G::SR * G::SW / 8; i += kThreads) reinterpret_cast<uint4*>(sc)[i] = make_uint4(0, 0, 0, 0);
-    const int n_items = cv.h->n_items;
+    // the decode kernel adds up the per-frame counts from zero
+    if (blockIdx.x == 0 && cv.h->counts)
+        for (int f = tid; f < cv.h->n_frames; f += kThreads) cv.h->counts[f] = 0;
+    __syncthreads();
+
+    if (warp == kConsumers / 32) {
+        // ---- producer warp: claims items, fills the ring, runs ahead ----
+        if (lane == 0) {
+            for (int t = 0;; ++t) {
+                const int b = t % NB;
+                if (t >= NB && !mbar_wait_bounded(&empty_bar[b], ((t / NB) - 1) & 1, kWaitLimitNs)) {
+                    atomicOr(status, kStatusTimeout);
+                    break;
+                }
+                const int it = atomicAdd(counter, 1);
+                ItemInfo& in = info[b];
+                in.id = it;
+                if (it >= n_items) {  // tell the consumers to stop
+                    mbar_arrive(&full_bar[b]);
+                    break;
+                }
+                const Item wi = decode_item<TH>(cv, it);
+                const FrameDesc& fd = cv.fds[wi.frame];
+                in.level = wi.level;
+                in.x0 = wi.tx * G::TW;
+                in.y0 = wi.ty * TH;
+                in.wk = fd.w >> wi.level;
+                in.hk = fd.h >> wi.level;
+                in.gw = fd.gw;
+                in.keys = fd.keys;
+                const CUtensorMap* map =
+                    wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
+                fence_tensormap_acquire(map);
+                mbar_arrive_expect_tx(&full_bar[b], G::BOX);
+                tma_load_2d(smem + G::IMG_OFF + b * G::BOXA, map, &full_bar[b], (in.x0 - 8) & ~15, in.y0 - 4);
+            }
+        }
+        return;
+    }
+
+    // ---- consumer warps ----
+    uint16_t* queue = reinterpret_cast<uint16_t*>(smem + G::Q_OFF) + warp * G::QCAP;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     const int thresh = cv.h->thresh, n_arc = cv.h->arc;
     const bool high_t = thresh >= 128;
     const bool three = n_arc >= 12;
     const uint32_t k7 = (uint32_t)((high_t ? 255 : 127) - thresh) * 0x01010101u;
 
-    // thread 0: takes the next item, publishes it and issues its TMA load
-    auto next_item = [&]() {
-        const int it = atomicAdd(counter, 1);
-        item_sh = it;
-        if (it < n_items) {
-            const Item wi = decode_item<TH>(cv, it);
-            cur_sh = wi;
-            const int x0 = wi.tx * G::TW, y0 = wi.ty * TH;
-            const CUtensorMap* map =
-                wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
-            fence_tensormap_acquire(map);
-            mbar_arrive_expect_tx(&bar, G::BOX);
-            tma_load_2d(img, map, &bar, (x0 - 8) & ~15, y0 - 4);
+    for (int t = 0;; ++t) {
+        const int b = t % NB;
+        if (!mbar_wait_bounded(&full_bar[b], (t / NB) & 1, kWaitLimitNs)) {
+            if (lane == 0) atomicOr(status, kStatusTimeout);
+            return;
         }
-    };
-    // the decode kernel adds up the per-frame counts from zero
-    if (blockIdx.x == 0 && cv.h->counts)
-        for (int f = tid; f < cv.h->n_frames; f += kThreads) cv.h->counts[f] = 0;
-    if (tid == 0) next_item();
-    __syncthreads();
-    uint32_t phase = 0;
-
-    for (;;) {
-        if (item_sh >= n_items) break;
-        const Item wi = cur_sh;
-        const FrameDesc& fd = cv.fds[wi.frame];
-        const int k = wi.level;
-        const int Wk = fd.w >> k, Hk = fd.h >> k;
-        const int x0 = wi.tx * G::TW, y0 = wi.ty * TH;
+        const ItemInfo in = info[b];
+        if (in.id >= n_items) break;
+        const uint8_t* img = smem + G::IMG_OFF + b * G::BOXA;
+        const int k = in.level, Wk = in.wk, Hk = in.hk, x0 = in.x0, y0 = in.y0;
         const uint32_t magic = cv.h->cell_magic[k];
         // score column 0 is level x = x0 - 4; box column 0 is ((x0 - 8) & ~15)
         const int xoff = x0 - 4 - ((x0 - 8) & ~15);  // 4 or 12
-        const bool ok = mbar_wait_bounded(&bar, phase, kWaitLimitNs);
-        phase ^= 1u;
-        if (!__syncthreads_and(ok)) {
-            if (tid == 0) atomicOr(status, kStatusTimeout);
-            return;
-        }
 
-        // 2. coarse test -> nibbles.  Rows/columns with no testable pixel
-        // (outside 3 <= x < Wk-3, 3 <= y < Hk-3) are skipped.
+        // 2. coarse test + compaction.  Testable pixels: 3 <= x < Wk-3, 3 <= y < Hk-3.
+        int total;
         {
             const int row_lo = max(0, 4 - y0), row_hi = min(G::SR, Hk - 2 - y0);
-            const int lx = x0 - 4 + 4 * lane;
-            const bool lane_ok = lx + 3 >= 3 && lx < Wk - 3;
+            const int lx = x0 - 4 + 8 * (lane & 15);  // level x of this lane's first pixel
+            uint32_t vm0 = 0, vm1 = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                vm0 |= (lx + j >= 3 && lx + j < Wk - 3) ? 0x80u << (8 * j) : 0u;
+                vm1 |= (lx + 4 + j >= 3 && lx + 4 + j < Wk - 3) ? 0x80u << (8 * j) : 0u;
+            }
+            const int xw = xoff / 4;
             if (high_t) {
-                if (three) coarse_rows<true, true, TH>(img, nib, xoff / 4, k7, warp, lane, row_lo, row_hi, lane_ok);
-                else coarse_rows<true, false, TH>(img, nib, xoff / 4, k7, warp, lane, row_lo, row_hi, lane_ok);
+                total = three ? coarse_and_compact<true, true, TH>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1)
+                              : coarse_and_compact<true, false, TH>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1);
             } else {
-                if (three) coarse_rows<false, true, TH>(img, nib, xoff / 4, k7, warp, lane, row_lo, row_hi, lane_ok);
-                else coarse_rows<false, false, TH>(img, nib, xoff / 4, k7, warp, lane, row_lo, row_hi, lane_ok);
+                total = three ? coarse_and_compact<false, true, TH>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1)
+                              : coarse_and_compact<false, false, TH>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1);
             }
         }
         __syncwarp();
 
-        // 3. warp-local compaction of this warp's rows (r = warp + 8 j):
-        // nibble word q holds row warp + 8 (q >> 3), pixels 16 (q & 7) .. +15
-        constexpr int WPL = G::RPW * 8 / 32;  // nibble words per lane
-        uint32_t words[WPL > 0 ? WPL : 1];
-        int cnt = 0;
-#pragma unroll
-        for (int j = 0; j < WPL; ++j) {
-            const int q = lane + 32 * j;
-            words[j] = reinterpret_cast<const uint32_t*>(nib + (warp + 8 * (q >> 3)) * 32)[q & 7];
-            cnt += __popc(words[j]);
-        }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        int pos = incl - cnt;
-#pragma unroll
-        for (int j = 0; j < WPL; ++j) {
-            uint32_t m = words[j];
-            const int q = lane + 32 * j;
-            const int base_idx = (warp + 8 * (q >> 3)) * G::SW + 16 * (q & 7);
-            while (m) {
-                const int b = __ffs(m) - 1;  // byte b >> 3, pixel b & 3 of that byte's word
-                m &= m - 1;
-                queue[pos++] = (uint16_t)(base_idx + 4 * (b >> 3) + (b & 7));
-            }
-        }
-        __syncwarp();
-
-        // 4. full test on this warp's queue; corners are compacted in place
+        // 3. full test on this warp's queue; corners are compacted in place
         int ncorner = 0;
+        const uint8_t* img_base = img + 3 * G::BW + xoff;
         for (int e0 = 0; e0 < total; e0 += 32) {
             const int e = e0 + lane;
             uint32_t s = 0;
             int idx = 0;
             if (e < total) {
                 idx = queue[e];
-                const int sr = idx >> 7, scx = idx & 127;
-                const int x = x0 - 4 + scx, y = y0 - 1 + sr;
-                if (x >= 3 && y >= 3 && x < Wk - 3 && y < Hk - 3)
-                    s = eval_corner<MODE, G::BW>(img + (3 + sr) * G::BW + xoff + scx, thresh, n_arc);
+                // box offset of score-region pixel (idx >> 7, idx & 127)
+                s = eval_corner<MODE, G::BW>(img_base + idx + 16 * (idx >> 7), thresh, n_arc);
             }
             const uint32_t cm = __ballot_sync(0xFFFFFFFFu, s != 0);
             if (s) {
@@ -531,12 +589,12 @@ __global__ void __launch_bounds__(kThreads) fast_nms_cell_kernel(const uint8_t* 
             }
             ncorner += __popc(cm);
         }
-        __syncthreads();  // all scores written; the image tile is free
+        // this warp is done with the image buffer
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_bar[b]);
+        named_barrier(1, kConsumers);  // all scores of the tile are written
 
-        // prefetch the next item into the image tile
-        if (tid == 0) next_item();
-
-        // 5. NMS on the corners, per-cell warp reduction, atomicMax
+        // 4. NMS on the corners, per-cell warp reduction, atomicMax
         for (int e0 = 0; e0 < ncorner; e0 += 32) {
             const int e = e0 + lane;
             uint32_t cell_id = 0xFFFFFFFFu;
@@ -552,33 +610,34 @@ __global__ void __launch_bounds__(kThreads) fast_nms_cell_kernel(const uint8_t* 
                                       s >= q[1] && s >= q[G::SW - 1] && s >= q[G::SW] && s >= q[G::SW + 1];
                     if (keep) {
                         const uint32_t x = (uint32_t)(x0 - 4 + scx), y = (uint32_t)(y0 - 1 + sr);
-                        cell_id = __umulhi(y, magic) * (uint32_t)fd.gw + __umulhi(x, magic);
+                        cell_id = __umulhi(y, magic) * (uint32_t)in.gw + __umulhi(x, magic);
                         hi = s;
                         lo = 0xFFFFFFFFu - (((uint32_t)k << 28) | (y * (uint32_t)Wk + x));
                     }
                 }
             }
-            // one max-reduction of the packed keys per distinct cell, led by
-            // its lowest lane, then one atomicMax per cell
-            uint32_t pend = __ballot_sync(0xFFFFFFFFu, hi != 0);
-            while (pend) {
-                const int leader = __ffs(pend) - 1;
+            const uint32_t surv = __ballot_sync(0xFFFFFFFFu, hi != 0);
+            if (surv) {
+                const int leader = __ffs(surv) - 1;
                 const uint32_t c = __shfl_sync(0xFFFFFFFFu, cell_id, leader);
-                const uint32_t grp = __ballot_sync(0xFFFFFFFFu, hi != 0 && cell_id == c);
-                if ((grp >> lane) & 1u) {
-                    const uint32_t hmax = __reduce_max_sync(grp, hi);
-                    const uint32_t lmax = __reduce_max_sync(grp, hi == hmax ? lo : 0u);
+                if (__all_sync(0xFFFFFFFFu, hi == 0 || cell_id == c)) {
+                    // one cell: max-reduce the packed keys over the warp, one atomic
+                    const uint32_t hmax = __reduce_max_sync(0xFFFFFFFFu, hi);
+                    const uint32_t lmax = __reduce_max_sync(0xFFFFFFFFu, hi == hmax ? lo : 0u);
                     if (lane == leader)
-                        atomicMax(reinterpret_cast<unsigned long long*>(&fd.keys[c]),
+                        atomicMax(reinterpret_cast<unsigned long long*>(&in.keys[c]),
                                   ((unsigned long long)hmax << 32) | lmax);
+                } else if (hi != 0) {
+                    atomicMax(reinterpret_cast<unsigned long long*>(&in.keys[cell_id]),
+                              ((unsigned long long)hi << 32) | lo);
                 }
-                pend &= ~grp;
             }
         }
-        __syncthreads();  // every warp's NMS has read its neighbours
+        named_barrier(1, kConsumers);  // every warp's NMS has read its neighbours
         for (int e = lane; e < ncorner; e += 32) sc[queue[e]] = 0;
-        // the next iteration's barrier (after its TMA wait) orders these
-        // resets before any score write of the next item
+        // the next tile's scores are written only after its coarse pass and a
+        // __syncwarp; the reset of another warp's rows is ordered by the
+        // named barrier that follows the next tile's full test
     }
 }
 

@@ -113,7 +113,7 @@ vio_status setup_device(int dev, DeviceSetup** out) {
             int occ = 0;
             if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TileGeom<kTH>::SMEM) !=
                     cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, TileGeom<kTH>::SMEM) != cudaSuccess)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, TileGeom<kTH>::SMEM) != cudaSuccess)
                 return VIO_ERR_CUDA;
             s.grid_fused[m] = (occ > 0 ? occ : 1) * s.sm_count;
         }
@@ -252,7 +252,7 @@ extern "C" vio_status vio_detect_noalloc(const uint8_t* frame, vio_dims d, int t
     if (cudaMemsetAsync(keys, 0, (size_t)gw * gh * 8, s) != cudaSuccess) return VIO_ERR_CUDA;
     noalloc_load_call<<<1, 256, 0, s>>>(blk, base + kCallOff, (int)bytes);
     if (levels > 1) pyr_fn(levels)<<<S->sm_count * 8, 256, 0, s>>>(base + kCallOff);
-    fused_fn(score)<<<S->grid_fused[score], 256, TileGeom<kTH>::SMEM, s>>>(base + kCallOff, counter, status);
+    fused_fn(score)<<<S->grid_fused[score], kThreads, TileGeom<kTH>::SMEM, s>>>(base + kCallOff, counter, status);
     noalloc_decode_kernel<<<S->sm_count * 4, 256, 0, s>>>(base + kCallOff, counter);
     return cudaGetLastError() == cudaSuccess ? VIO_OK : VIO_ERR_CUDA;
 }
