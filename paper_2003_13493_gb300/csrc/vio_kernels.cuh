@@ -227,12 +227,15 @@ __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, i
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * P + circ_dx(i)];
     const uint32_t K = ((0x7FFFu - c - (uint32_t)t) & 0xFFFFu) | ((0x7FFFu + c - (uint32_t)t) << 16);
-    uint32_t acc = 0;
+    // four independent chains (points i = 4j + q, q = 0..3) shifted by 4
+    // per step leave point i's flags at bits i + 3 - q, merged below
+    uint32_t a[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const uint32_t w = K + v[i] * 0xFFFF0001u;
-        acc = (acc >> 1) | (w & 0x80008000u);
+        a[i & 3] = (a[i & 3] >> 4) | (w & 0x80008000u);
     }
+    const uint32_t acc = (a[0] >> 3) | (a[1] >> 2) | (a[2] >> 1) | a[3];
     const uint32_t bm = acc & 0xFFFFu, dm = acc >> 16;
     // at most one polarity can hold n >= 9 points
     const bool bright = __popc(bm) >= n;
@@ -461,7 +464,7 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
 }
 
 template <int TH, int MODE>
-__global__ void __launch_bounds__(kThreads) fast_nms_cell_kernel(const uint8_t* __restrict__ call,
+__global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_t* __restrict__ call,
                                                                  int32_t* __restrict__ counter,
                                                                  uint32_t* __restrict__ status) {
     using G = TileGeom<TH>;
@@ -552,13 +555,17 @@ __global__ void __launch_bounds__(kThreads) fast_nms_cell_kernel(const uint8_t* 
         int total;
         {
             const int row_lo = max(0, 4 - y0), row_hi = min(G::SR, Hk - 2 - y0);
-            const int lx = x0 - 4 + 8 * (lane & 15);  // level x of this lane's first pixel
+            // NMS needs scores of score columns 3..124 (x0-1 .. x0+120) only
+            const int sx = 8 * (lane & 15);           // score column of this lane's first pixel
+            const int lx = x0 - 4 + sx;               // its level x
+            const int xlo = max(3, 3 - x0 + 4), xhi = min(125, Wk - 3 - x0 + 4);  // kept score columns [xlo, xhi)
             uint32_t vm0 = 0, vm1 = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                vm0 |= (lx + j >= 3 && lx + j < Wk - 3) ? 0x80u << (8 * j) : 0u;
-                vm1 |= (lx + 4 + j >= 3 && lx + 4 + j < Wk - 3) ? 0x80u << (8 * j) : 0u;
+                vm0 |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
+                vm1 |= (sx + 4 + j >= xlo && sx + 4 + j < xhi) ? 0x80u << (8 * j) : 0u;
             }
+            (void)lx;
             const int xw = xoff / 4;
             if (high_t) {
                 total = three ? coarse_and_compact<true, true, TH>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1)
@@ -579,15 +586,22 @@ __global__ void __launch_bounds__(kThreads) fast_nms_cell_kernel(const uint8_t* 
             int idx = 0;
             if (e < total) {
                 idx = queue[e];
-                // box offset of score-region pixel (idx >> 7, idx & 127)
-                s = eval_corner<MODE, G::BW>(img_base + idx + 16 * (idx >> 7), thresh, n_arc);
+                // box offset of score-region pixel (idx >> 7, idx & 127); SAD-B
+                // is scored below, on the corners only
+                s = eval_corner<MODE, G::BW, MODE != 0>(img_base + idx + 16 * (idx >> 7), thresh, n_arc);
             }
             const uint32_t cm = __ballot_sync(0xFFFFFFFFu, s != 0);
             if (s) {
-                sc[idx] = (uint16_t)s;
+                if (MODE != 0) sc[idx] = (uint16_t)s;
                 queue[ncorner + __popc(cm & lt_mask)] = (uint16_t)idx;
             }
             ncorner += __popc(cm);
+        }
+        if (MODE == 0) {
+            for (int e = lane; e < ncorner; e += 32) {
+                const int idx = queue[e];
+                sc[idx] = (uint16_t)sad_b<G::BW>(img_base + idx + 16 * (idx >> 7));
+            }
         }
         // this warp is done with the image buffer
         __syncwarp();
