@@ -391,13 +391,13 @@ struct ItemInfo {
 };
 
 template <int TH>
-__device__ __forceinline__ Item decode_item(const CallView& cv, int it) {
+__device__ __forceinline__ Item decode_item(const CallView& cv, const int32_t* tiles, int it) {
     const int n = cv.h->n_frames, L = cv.h->levels;
-    const int j = upper_index(cv.tiles, n * L, it);
+    const int j = upper_index(tiles, n * L, it);
     Item r;
     r.frame = j % n;
     r.level = L - 1 - j / n;
-    const int t = it - cv.tiles[j];
+    const int t = it - tiles[j];
     const int wk = cv.fds[r.frame].w >> r.level;
     const int ntx = (wk + TileGeom<TH>::TW - 1) / TileGeom<TH>::TW;
     r.ty = t / ntx;
@@ -472,6 +472,9 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
     extern __shared__ __align__(128) uint8_t smem_raw[];
     __shared__ uint64_t full_bar[NB], empty_bar[NB];
     __shared__ ItemInfo info[NB];
+    // the tile table, copied once so that the producer's search stays on chip
+    constexpr int kTileCache = 512;
+    __shared__ int32_t tiles_sh[kTileCache];
     // TMA destinations must be 128-byte aligned
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint16_t* sc = reinterpret_cast<uint16_t*>(smem + G::SC_OFF);
@@ -492,25 +495,32 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
     // the decode kernel adds up the per-frame counts from zero
     if (blockIdx.x == 0 && cv.h->counts)
         for (int f = tid; f < cv.h->n_frames; f += kThreads) cv.h->counts[f] = 0;
+    const int n_tiles = cv.h->n_frames * cv.h->levels + 1;
+    const bool cached = n_tiles <= kTileCache;
+    if (cached)
+        for (int i = tid; i < n_tiles; i += kThreads) tiles_sh[i] = cv.tiles[i];
     __syncthreads();
 
     if (warp == kConsumers / 32) {
         // ---- producer warp: claims items, fills the ring, runs ahead ----
         if (lane == 0) {
+            const int32_t* tiles = cached ? tiles_sh : cv.tiles;
+            int claimed = atomicAdd(counter, 1);  // claimed one item ahead of its use
             for (int t = 0;; ++t) {
                 const int b = t % NB;
+                const int it = claimed;
+                if (it < n_items) claimed = atomicAdd(counter, 1);
                 if (t >= NB && !mbar_wait_bounded(&empty_bar[b], ((t / NB) - 1) & 1, kWaitLimitNs)) {
                     atomicOr(status, kStatusTimeout);
                     break;
                 }
-                const int it = atomicAdd(counter, 1);
                 ItemInfo& in = info[b];
                 in.id = it;
                 if (it >= n_items) {  // tell the consumers to stop
                     mbar_arrive(&full_bar[b]);
                     break;
                 }
-                const Item wi = decode_item<TH>(cv, it);
+                const Item wi = decode_item<TH>(cv, tiles, it);
                 const FrameDesc& fd = cv.fds[wi.frame];
                 in.level = wi.level;
                 in.x0 = wi.tx * G::TW;
