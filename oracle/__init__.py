@@ -60,6 +60,9 @@ def _load():
         lib.oracle_score_pixel.restype = ci
         lib.oracle_score_map.argtypes = [u8p, ci, ci, ci, ci, ci, ci, i32p]
         lib.oracle_nms3.argtypes = [i32p, ci, ci, i32p]
+        lib.oracle_nms.argtypes = [i32p, ci, ci, ci, i32p]
+        lib.oracle_detect_nms.argtypes = [u8p, ci, ci, ci, ci, ci, ci, ci, ci, ci, i32p]
+        lib.oracle_detect_nms.restype = ci
         lib.oracle_num_cells.argtypes = [ci, ci, ci]
         lib.oracle_num_cells.restype = ci
         lib.oracle_detect.argtypes = [u8p, ci, ci, ci, ci, ci, ci, ci, ci, i32p]
@@ -140,18 +143,26 @@ def nms3(score: np.ndarray) -> np.ndarray:
     return out
 
 
+def nms(score: np.ndarray, radius: int) -> np.ndarray:
+    s = np.ascontiguousarray(score, dtype=np.int32)
+    h, w = s.shape
+    out = np.zeros_like(s)
+    _load().oracle_nms(_i32(s), w, h, radius, _i32(out))
+    return out
+
+
 def num_cells(w: int, h: int, cell: int) -> int:
     return int(_load().oracle_num_cells(w, h, cell))
 
 
 def detect(img: np.ndarray, thresh: int, n_arc: int, cell: int, levels: int,
-           mode: int = SAD_B) -> tuple[np.ndarray, int]:
+           mode: int = SAD_B, nms_radius: int = 1) -> tuple[np.ndarray, int]:
     """Per-cell features ``(ncells, 4)`` int32 rows (x, y, level, score) and
-    the number of non-empty cells."""
+    the number of non-empty cells; NMS over (2 nms_radius + 1)^2 windows."""
     img = _img(img)
     h, w = img.shape
     out = np.zeros((num_cells(w, h, cell), 4), dtype=np.int32)
-    n = _load().oracle_detect(_u8(img), w, h, w, thresh, n_arc, cell, levels, mode, _i32(out))
+    n = _load().oracle_detect_nms(_u8(img), w, h, w, thresh, n_arc, cell, levels, mode, nms_radius, _i32(out))
     if n < 0:
         raise MemoryError("oracle_detect: allocation failed")
     return out, int(n)

@@ -20,7 +20,8 @@
  *                    all darker or all brighter; a 3-pixel border skipped.
  *   scores           Section II-D: SAD-B, SAD-A, MT; 0 when the test fails.
  *   NMS              Algorithm 1, "per scale"; Section I-B (Moore
- *                    neighbourhood, n = 1 gives 3x3).
+ *                    neighbourhood of side 2n+1: n = 1 gives 3x3, n = 2..4
+ *                    the 5x5..9x9 windows of Table III).
  *   NMS-C            Algorithm 1 (after all scales), Section II-B (one
  *                    feature per cell, the highest score) and Section II-C
  *                    (one grid for all levels, level-k positions scaled
@@ -174,14 +175,16 @@ void oracle_score_map(const uint8_t* img, int w, int h, int pitch, int thresh, i
             out[y * w + x] = oracle_score_pixel(img, w, h, pitch, x, y, thresh, n_arc, mode);
 }
 
-/* 3x3 NMS on a dense w x h score map (row pitch w). */
-void oracle_nms3(const int32_t* s, int w, int h, int32_t* out) {
+/* NMS over the (2n+1) x (2n+1) Moore neighbourhood (Section I-B; n = 1 is
+ * the 3x3 case of Algorithm 1, n = 2..4 the larger windows of Table III) on
+ * a dense w x h score map (row pitch w). */
+void oracle_nms(const int32_t* s, int w, int h, int n, int32_t* out) {
     for (int y = 0; y < h; ++y) {
         for (int x = 0; x < w; ++x) {
             int v = s[y * w + x];
             int keep = v > 0;
-            for (int dy = -1; dy <= 1 && keep; ++dy) {
-                for (int dx = -1; dx <= 1; ++dx) {
+            for (int dy = -n; dy <= n && keep; ++dy) {
+                for (int dx = -n; dx <= n; ++dx) {
                     if (dx == 0 && dy == 0) continue;
                     int xx = x + dx, yy = y + dy;
                     int nv = (xx >= 0 && yy >= 0 && xx < w && yy < h) ? s[yy * w + xx] : 0;
@@ -195,6 +198,8 @@ void oracle_nms3(const int32_t* s, int w, int h, int32_t* out) {
         }
     }
 }
+
+void oracle_nms3(const int32_t* s, int w, int h, int32_t* out) { oracle_nms(s, w, h, 1, out); }
 
 /* Is candidate (s1, k1, y1, x1) a better cell winner than (s0, k0, y0, x0)? */
 static int better(int s1, int k1, int y1, int x1, int s0, int k0, int y0, int x0) {
@@ -213,8 +218,8 @@ int oracle_num_cells(int w, int h, int cell) {
  * over the ceil(w/cell) x ceil(h/cell) level-0 grid: x, y, level, score.
  * Returns the number of non-empty cells, or -1 on allocation failure.
  */
-int oracle_detect(const uint8_t* img, int w, int h, int pitch, int thresh, int n_arc, int cell,
-                  int levels, int mode, int32_t* out) {
+int oracle_detect_nms(const uint8_t* img, int w, int h, int pitch, int thresh, int n_arc, int cell,
+                      int levels, int mode, int nms_radius, int32_t* out) {
     int gw = (w + cell - 1) / cell, gh = (h + cell - 1) / cell;
     int ncell = gw * gh;
     for (int i = 0; i < ncell; ++i) {
@@ -252,7 +257,7 @@ int oracle_detect(const uint8_t* img, int w, int h, int pitch, int thresh, int n
             hk >>= 1;
         }
         oracle_score_map(lev, wk, hk, wk, thresh, n_arc, mode, sc);
-        oracle_nms3(sc, wk, hk, nm);
+        oracle_nms(sc, wk, hk, nms_radius, nm);
         for (int y = 0; y < hk; ++y) {
             for (int x = 0; x < wk; ++x) {
                 int s = nm[y * wk + x];
@@ -279,4 +284,9 @@ int oracle_detect(const uint8_t* img, int w, int h, int pitch, int thresh, int n
     int cnt = 0;
     for (int i = 0; i < ncell; ++i) cnt += out[4 * i + 2] >= 0;
     return cnt;
+}
+
+int oracle_detect(const uint8_t* img, int w, int h, int pitch, int thresh, int n_arc, int cell, int levels,
+                  int mode, int32_t* out) {
+    return oracle_detect_nms(img, w, h, pitch, thresh, n_arc, cell, levels, mode, 1, out);
 }

@@ -98,25 +98,34 @@ def pyramid(img, levels):
     return [o.astype(np.uint8) for o in out]
 
 
-NEIGHBOURS = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy) != (0, 0)]
+def neighbours(radius):
+    return [(dx, dy) for dy in range(-radius, radius + 1) for dx in range(-radius, radius + 1)
+            if (dx, dy) != (0, 0)]
 
 
-def nms3(s):
+NEIGHBOURS = neighbours(1)
+
+
+def nms(s, radius=1):
     h, w = len(s), len(s[0])
     out = [[0] * w for _ in range(h)]
+    nbs = neighbours(radius)
     for y in range(h):
         for x in range(w):
             v = s[y][x]
             if v <= 0:
                 continue
-            nb = [s[y + dy][x + dx] if 0 <= x + dx < w and 0 <= y + dy < h else 0
-                  for dx, dy in NEIGHBOURS]
+            nb = [s[y + dy][x + dx] if 0 <= x + dx < w and 0 <= y + dy < h else 0 for dx, dy in nbs]
             if all(v >= q for q in nb):
                 out[y][x] = v
     return out
 
 
-def detect(img, t, n, cell, levels, mode=0):
+def nms3(s):
+    return nms(s, 1)
+
+
+def detect(img, t, n, cell, levels, mode=0, radius=1):
     img = np.asarray(img, dtype=np.uint8)
     h, w = img.shape
     gw, gh = -(-w // cell), -(-h // cell)
@@ -125,7 +134,7 @@ def detect(img, t, n, cell, levels, mode=0):
         L = lev.tolist()
         hk, wk = len(L), len(L[0]) if L else 0
         sm = [[score(L, x, y, t, n, mode) for x in range(wk)] for y in range(hk)]
-        m = nms3(sm) if hk and wk else []
+        m = nms(sm, radius) if hk and wk else []
         for y in range(hk):
             for x in range(wk):
                 if m[y][x] > 0:

@@ -331,3 +331,35 @@ def test_empty_and_degenerate(oracle_mod):
     tiny[3, 3] = 200
     feats, cnt = oracle_mod.detect(tiny, 10, 9, 32, 1)
     assert cnt == 1 and tuple(feats[0]) == (3, 3, 0, 16 * 200)
+
+
+# ---- larger NMS windows (Section I-B, Table III: n = 2..4) -----------------
+
+
+@pytest.mark.parametrize("radius", [2, 3, 4])
+def test_larger_nms_windows_match_naive(oracle_mod, radius):
+    rng = np.random.default_rng(radius)
+    for i in range(8):
+        h, w = int(rng.integers(7, 30)), int(rng.integers(7, 30))
+        img = (rng.integers(0, 5, size=(h, w)) * 50).astype(np.uint8) if i % 2 else \
+            make_frame(w, h, seed=300 + i, n_shapes=4)
+        sm = oracle_mod.score_map(img, 10, 9, 0)
+        assert np.array_equal(oracle_mod.nms(sm, radius), np.array(naive.nms(sm.tolist(), radius)))
+        levels = 2 if min(w, h) >= 14 else 1
+        got, _ = oracle_mod.detect(img, 10, 9, 32, levels, 0, radius)
+        assert np.array_equal(got, naive.detect(img, 10, 9, 32, levels, 0, radius))
+
+
+def test_nms_windows_nest_and_match_the_3x3_entry(oracle_mod):
+    img = make_frame(200, 150, seed=42, n_shapes=12)
+    sm = oracle_mod.score_map(img, 12, 9, 0)
+    assert np.array_equal(oracle_mod.nms(sm, 1), oracle_mod.nms3(sm))
+    prev = oracle_mod.nms(sm, 1) > 0
+    for r in (2, 3, 4):
+        cur = oracle_mod.nms(sm, r) > 0
+        assert not (cur & ~prev).any()  # a wider window only removes survivors
+        prev = cur
+    # the 3x3 detection equals the default entry point
+    a, _ = oracle_mod.detect(img, 12, 9, 32, 2)
+    b, _ = oracle_mod.detect(img, 12, 9, 32, 2, 0, 1)
+    assert np.array_equal(a, b)
