@@ -34,6 +34,10 @@ WORKLOADS = {
                     desc="64 frames in one batched launch: 16 each of 640x480, 752x480, 1280x720, "
                          "1920x1080 (seeds 2..65, 40 shapes), 3-level pyramid, FAST-9, thresh 15, "
                          "3x3 NMS, 32x32 cells, SAD-B"),
+    "large4k": dict(levels=4, thresh=10, arc=9, cell=64, sweep=[(t, a) for a in (12, 9) for t in (5, 10, 20, 40)],
+                    desc="32 frames of 3840x2160 (seeds 100..131, 400 shapes), 4-level pyramid built once, "
+                         "FAST-12 and FAST-9 at thresholds 5, 10, 20, 40 (8 detections per step), 3x3 NMS, "
+                         "64x64 cells, SAD-B"),
     "single752": dict(levels=3, thresh=20, arc=9, cell=32,
                       desc="one 752x480 frame (seed 1), 3-level pyramid, FAST-9, thresh 20, 3x3 NMS, "
                            "32x32 cells, SAD-B"),
@@ -62,6 +66,8 @@ def make_frames(workload: str):
 
     if workload == "mixed64":
         return synth.mixed_batch(first_seed=2, per_size=16)
+    if workload == "large4k":
+        return [synth.make_frame(3840, 2160, seed=100 + i, n_shapes=400) for i in range(32)]
     return [synth.make_frame(752, 480, seed=1)]
 
 
@@ -148,6 +154,26 @@ def recorded_traffic(workload: str):
     return traffic if src == kernel_source_hash() else None
 
 
+def max_over_ranks(value: float) -> float:
+    """Largest `value` over all ranks (identity without torch.distributed).
+    Uses a CUDA tensor under NCCL and a CPU tensor otherwise (gloo)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(units_per_rank: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput: every rank did units_per_rank per step; the job
+    took the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -187,15 +213,20 @@ def oracle_rate(frames, wl, seconds: float):
 
 # ---- our implementation ------------------------------------------------------------
 
-def algorithmic_bytes(dims, levels, cell, num_cells):
-    """Per-step bytes and the fused kernel's bytes per launch."""
+def algorithmic_bytes(dims, levels, cell, num_cells, npar=1):
+    """Per-step bytes and the fused kernel's bytes per launch.
+
+    A step reads level 0 once, writes and reads each pyramid level once and
+    writes 16 bytes per cell; with npar detections over the same pyramid each
+    further detection re-reads every level and writes its own cells.  The
+    fused kernel reads every level once and updates 8 bytes of key per cell."""
     step = 0.0
     fused = 0.0
     for (w, h) in dims:
         nc = num_cells(w, h, cell)
         pyr_px = sum((w >> k) * (h >> k) for k in range(1, levels))
         all_px = sum((w >> k) * (h >> k) for k in range(levels))
-        step += w * h + 2 * pyr_px + 16 * nc
+        step += w * h + 2 * pyr_px + (npar - 1) * all_px + npar * 16 * nc
         fused += all_px + 8 * nc
     return step, fused
 
@@ -214,7 +245,8 @@ def run_ours(args, rank, world, local_rank):
     n = len(frames_np)
     dims = [(f.shape[1], f.shape[0]) for f in frames_np]
     mpx = sum(w * h for w, h in dims) / 1e6
-    sets = 4 if args.workload == "mixed64" else 64
+    # enough device copies that the inputs of a step are not in L2 (129 MB)
+    sets = max(1, -(-200 // max(1, int(mpx))))
     stream = torch.cuda.Stream(device=dev)
     sh = ctypes.c_void_p(stream.cuda_stream)
 
@@ -225,8 +257,11 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         for _ in range(sets):
             dev_sets.append([torch.from_numpy(f).to(dev) for f in frames_np])
-    outs = [torch.empty((vio.num_cells(w, h, wl["cell"]), 4), dtype=torch.int32, device=dev) for w, h in dims]
-    counts = torch.empty(n, dtype=torch.int32, device=dev)
+    sweep = wl.get("sweep")
+    npar = len(sweep) if sweep else 1
+    outs = [torch.empty((vio.num_cells(w, h, wl["cell"]), 4), dtype=torch.int32, device=dev)
+            for _ in range(npar) for w, h in dims]
+    counts = torch.empty(npar * n, dtype=torch.int32, device=dev)
 
     def marshal(frames):
         d = (vio.Dims * n)(*[vio.Dims(f.shape[1], f.shape[0], f.stride(0)) for f in frames])
@@ -234,12 +269,18 @@ def run_ours(args, rank, world, local_rank):
         return fp, d
 
     marshalled = [marshal(s) for s in dev_sets]
-    optr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    optr = (ctypes.c_void_p * (npar * n))(*[o.data_ptr() for o in outs])
     cptr = ctypes.c_void_p(counts.data_ptr())
+    if sweep:
+        th = (ctypes.c_int * npar)(*[p[0] for p in sweep])
+        ar = (ctypes.c_int * npar)(*[p[1] for p in sweep])
 
     def step(i, d=det):
         fp, dd = marshalled[i % sets]
-        d.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], optr, cptr, sh)
+        if sweep:
+            d.detect_sweep_ptrs(fp, dd, n, th, ar, npar, wl["cell"], wl["levels"], optr, cptr, sh)
+        else:
+            d.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], optr, cptr, sh)
 
     for i in range(max(3, args.warmup)):
         step(i)
@@ -273,14 +314,10 @@ def run_ours(args, rank, world, local_rank):
     clocks.mark("t1")
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1))
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     ms_per_step = ms / args.steps
-    fps = world * n * args.steps / (ms / 1e3)
+    fps = weak_scaling_rate(n, args.steps, ms, world)
 
     res = {
         "metric": METRIC, "value": round(fps, 1), "unit": "frames/s", "n_gpus": world,
@@ -289,6 +326,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded value noise + shapes, integer generator)",
         "mpixel_per_s": round(world * mpx * args.steps / (ms / 1e3), 1),
         "config": {"workload": f"{args.workload}: {wl['desc']}", "frames_per_step": n,
+                   "detections_per_frame": npar,
                    "mpixel_per_step": round(mpx, 3), "levels": wl["levels"], "thresh": wl["thresh"],
                    "arc_len": wl["arc"], "cell": wl["cell"], "score": "SAD-B",
                    "l2": f"inputs rotate over {sets} device copies of the batch "
@@ -297,8 +335,10 @@ def run_ours(args, rank, world, local_rank):
                             "picked_by": "autotuner" if args.variant < 0 else "--variant"},
                    "parallelism": f"replicas x{world}, no collective"},
         "clocks": clk,
-        "gpu_launches": args.steps * (3 if wl["levels"] > 1 else 2),
+        "gpu_launches": args.steps * ((1 if wl["levels"] > 1 else 0) + 2 * npar),
     }
+    if sweep:
+        res["detections_per_s"] = round(world * n * npar * args.steps / (ms / 1e3), 1)
     if rank == 0 and not args.no_extras:
         res.update(extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cptr, n, mpx,
                           ms_per_step))
@@ -319,15 +359,20 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     prof.set_variant(det.tuning()[2])
     steps = min(args.steps, 200)
     acc = [0.0, 0.0, 0.0]
+    sweep = wl.get("sweep")
+    npar = len(sweep) if sweep else 1
     for i in range(steps + 3):
         fp, dd = marshalled[i % len(marshalled)]
-        prof.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], optr, cptr, sh)
+        # one detection per step here (the first setting of a sweep): the
+        # stage events time each kernel of that launch
+        t0, a0 = (sweep[0] if sweep else (wl["thresh"], wl["arc"]))
+        prof.detect_ptrs(fp, dd, n, t0, a0, wl["cell"], wl["levels"], optr, cptr, sh)
         st = prof.stage_ms()
         if i >= 3:
             acc = [a + b for a, b in zip(acc, st)]
     prof.close()
     stage = [a / steps for a in acc]
-    step_bytes, fused_bytes = algorithmic_bytes(dims, wl["levels"], wl["cell"], vio.num_cells)
+    step_bytes, fused_bytes = algorithmic_bytes(dims, wl["levels"], wl["cell"], vio.num_cells, npar)
     peaks, kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = fused_bytes / (stage[1] * 1e-3) / 1e9
@@ -342,6 +387,9 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     out["step_roofline"] = {"algorithmic_bytes_per_step": int(step_bytes), "achieved_gbs": round(step_gbs, 1),
                             "frac": round(step_gbs / peak, 4),
                             "what": "whole step (pyramid + fused detect + decode) against the HBM peak"}
+
+    if sweep:
+        return out
 
     # plain path: one frame per call
     plain = vio.Detector(device=dev.index, max_frames=4)

@@ -148,6 +148,23 @@ vio_status vio_detect(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims
                       vio_feature* const* out_cells, int32_t* out_counts, vio_stream stream);
 
 /*
+ * Parameter sweep over one set of frames: detection p (p < n_params) uses
+ * thresholds[p] and arc_lens[p] and gives exactly what vio_detect would;
+ * the pyramid is built once and read by every detection.
+ *
+ *   thresholds, arc_lens  host int[n_params], 1 <= n_params <= 64
+ *   out_cells             host array of n_params * n_frames DEVICE pointers,
+ *                         parameter-major: entry p * n_frames + i is frame i
+ *                         of detection p
+ *   out_counts            DEVICE int32[n_params * n_frames] (same order) or NULL
+ *
+ * Other arguments, checks and errors as vio_detect.  Asynchronous on `stream`.
+ */
+vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims* dims, int n_frames,
+                            const int* thresholds, const int* arc_lens, int n_params, int cell_size, int levels,
+                            vio_feature* const* out_cells, int32_t* out_counts, vio_stream stream);
+
+/*
  * Same as vio_detect for frames and results in HOST memory: the frames are
  * copied into resident device slots, detected, and the cells copied back;
  * the call returns when out_cells (host, per frame) and out_counts (host

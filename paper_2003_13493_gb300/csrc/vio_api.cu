@@ -256,7 +256,7 @@ ShapeKey shape_key(const vio_dims* dims, int n, int cell, int levels) {
 
 // Enqueues pyramid -> fused detect -> decode on `s`; launch shapes depend only
 // on the context (the kernels read the batch from the call block).
-vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s) {
+vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s, bool pyramid = true) {
     const Variant& v = variants()[variant];
     const int mode = ctx->cfg.score;
     const bool prof = ctx->cfg.profile != 0;
@@ -265,7 +265,7 @@ vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s
     if (prof) VIO_CK(cudaStreamIsCapturing(s, &cap));
     const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[0], s, rec_flags));
-    if (levels > 1) {
+    if (levels > 1 && pyramid) {
         pyr_fn(levels)<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->d_call);
         VIO_CK(cudaGetLastError());
     }
@@ -285,15 +285,17 @@ vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s
     return VIO_OK;
 }
 
-vio_status get_graph(vio_ctx* ctx, int variant, int levels, cudaGraphExec_t* out) {
-    cudaGraphExec_t& g = ctx->graphs[variant][levels];
+// Graph slot `levels` holds pyramid -> detect -> decode; slot 0 holds
+// detect -> decode alone (the pyramid is already in place).
+vio_status get_graph(vio_ctx* ctx, int variant, int levels, bool pyramid, cudaGraphExec_t* out) {
+    cudaGraphExec_t& g = ctx->graphs[variant][pyramid ? levels : 0];
     if (!g) {
         // the launch attributes are set outside the capture
         const Variant& v = variants()[variant];
         VIO_CK(cudaFuncSetAttribute(v.fn[ctx->cfg.score], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
         cudaGraph_t graph = nullptr;
         VIO_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        vio_status es = enqueue_kernels(ctx, variant, levels, ctx->capture_stream);
+        vio_status es = enqueue_kernels(ctx, variant, levels, ctx->capture_stream, pyramid);
         cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (es != VIO_OK) return es;
         VIO_CK(ce);
@@ -308,7 +310,7 @@ vio_status get_graph(vio_ctx* ctx, int variant, int levels, cudaGraphExec_t* out
 // it and launches the three kernels on `s`.
 vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims,
                   int n, int thresh, int arc, int cell, int levels, int4* const* outs, int32_t* counts,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool pyramid = true) {
     const Variant& v = variants()[variant];
     // arena layout
     size_t koff = 0, poff = 0;
@@ -427,9 +429,9 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
     VIO_CK(cudaEventRecord(ctx->ring_ev[slot], s));
     if (ctx->cfg.use_graphs) {
         cudaGraphExec_t g = nullptr;
-        if ((st = get_graph(ctx, variant, levels, &g)) != VIO_OK) return st;
+        if ((st = get_graph(ctx, variant, levels, pyramid, &g)) != VIO_OK) return st;
         VIO_CK(cudaGraphLaunch(g, s));
-    } else if ((st = enqueue_kernels(ctx, variant, levels, s)) != VIO_OK) {
+    } else if ((st = enqueue_kernels(ctx, variant, levels, s, pyramid)) != VIO_OK) {
         return st;
     }
     VIO_CK(cudaEventRecord(ctx->last_ev, s));
@@ -658,6 +660,69 @@ vio_status vio_detect(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims
     for (int i = 0; i < n; ++i) outs[i] = reinterpret_cast<int4*>(out_cells[i]);
     return detect_impl(ctx, lev0.data(), pitch0.data(), dims, n, thresh, arc, cell, levels, outs.data(), out_counts,
                        s);
+}
+
+vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims* dims, int n,
+                            const int* thresholds, const int* arc_lens, int n_params, int cell, int levels,
+                            vio_feature* const* out_cells, int32_t* out_counts, vio_stream stream) {
+    if (!ctx) return VIO_ERR_INVALID_ARG;
+    if (!thresholds || !arc_lens || n_params < 1 || n_params > 64)
+        return fail(ctx, VIO_ERR_INVALID_ARG, "n_params must be in 1..64 with thresholds and arc lengths");
+    vio_status st;
+    for (int p = 0; p < n_params; ++p)
+        if ((st = check_args(ctx, frames, dims, n, thresholds[p], arc_lens[p], cell, levels, out_cells)) != VIO_OK)
+            return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    VIO_CK(cudaSetDevice(ctx->cfg.device));
+    for (int i = 0; i < n_params * n; ++i)
+        if (!out_cells[i]) return fail(ctx, VIO_ERR_INVALID_ARG, "NULL output pointer");
+    for (int i = 0; i < n; ++i)
+        if (!frames[i]) return fail(ctx, VIO_ERR_INVALID_ARG, "NULL frame pointer");
+    // frames that TMA cannot address directly are staged into aligned slots
+    std::vector<const uint8_t*> lev0(frames, frames + n);
+    std::vector<int> pitch0(n);
+    size_t need = 0;
+    std::vector<size_t> off(n, (size_t)-1);
+    for (int i = 0; i < n; ++i) {
+        pitch0[i] = dims[i].pitch;
+        if (((uintptr_t)frames[i] & 15) || (dims[i].pitch & 15)) {
+            off[i] = need;
+            need += align_up((size_t)align_up(dims[i].w, 16) * dims[i].h, 256);
+        }
+    }
+    if (need) {
+        if ((st = grow(ctx, (void**)&ctx->d_in, &ctx->in_cap, need, false)) != VIO_OK) return st;
+        for (int i = 0; i < n; ++i)
+            if (off[i] != (size_t)-1) {
+                const int p = (int)align_up(dims[i].w, 16);
+                VIO_CK(cudaMemcpy2DAsync(ctx->d_in + off[i], p, frames[i], dims[i].pitch, dims[i].w, dims[i].h,
+                                         cudaMemcpyDeviceToDevice, s));
+                lev0[i] = ctx->d_in + off[i];
+                pitch0[i] = p;
+            }
+    }
+    int vi = ctx->pinned_variant >= 0 ? ctx->pinned_variant : 0;
+    if (ctx->pinned_variant < 0 && ctx->cfg.autotune) {
+        const ShapeKey key = shape_key(dims, n, cell, levels);
+        if (!ctx->tuned.count(key)) {
+            std::vector<int4*> outs0(n);
+            for (int i = 0; i < n; ++i) outs0[i] = reinterpret_cast<int4*>(out_cells[i]);
+            if ((st = autotune(ctx, key, lev0.data(), pitch0.data(), dims, n, thresholds[0], arc_lens[0], cell,
+                               levels, outs0.data(), out_counts, s)) != VIO_OK)
+                return st;
+        }
+        vi = ctx->tuned[key];
+    }
+    ctx->last_variant = vi;
+    // the pyramid is built by the first detection and read by all of them
+    std::vector<int4*> outs(n);
+    for (int p = 0; p < n_params; ++p) {
+        for (int i = 0; i < n; ++i) outs[i] = reinterpret_cast<int4*>(out_cells[(size_t)p * n + i]);
+        if ((st = launch(ctx, vi, lev0.data(), pitch0.data(), dims, n, thresholds[p], arc_lens[p], cell, levels,
+                         outs.data(), out_counts ? out_counts + (size_t)p * n : nullptr, s, p == 0)) != VIO_OK)
+            return st;
+    }
+    return VIO_OK;
 }
 
 vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims, int n, int thresh,

@@ -103,6 +103,9 @@ def load(build_if_missing: bool = True):
     lib.vio_detect.restype = st
     lib.vio_detect_host.argtypes = detect_args
     lib.vio_detect_host.restype = st
+    lib.vio_detect_sweep.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(Dims), ci, ctypes.POINTER(ci),
+                                     ctypes.POINTER(ci), ci, ci, ci, ctypes.POINTER(P), P, P]
+    lib.vio_detect_sweep.restype = st
     lib.vio_sync.argtypes = [P, P]
     lib.vio_sync.restype = st
     lib.vio_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
@@ -220,6 +223,34 @@ class Detector:
         self._check(self.lib.vio_detect(self.ctx, fptr, dims, n, thresh, arc_len, cell, levels, optr,
                                         ctypes.c_void_p(counts.data_ptr()), _stream_handle(stream)))
         return outs, counts
+
+    def detect_sweep(self, frames, params, cell: int, levels: int, stream=None):
+        """params: list of (thresh, arc_len).  Returns (outs[p][i] tensors, counts (n_params, n))."""
+        import torch
+
+        n, npar = len(frames), len(params)
+        dims = (Dims * n)()
+        fptr = (ctypes.c_void_p * n)()
+        for i, f in enumerate(frames):
+            if f.dtype != torch.uint8 or f.dim() != 2 or f.stride(1) != 1 or not f.is_cuda:
+                raise ValueError("frames must be 2-D uint8 CUDA tensors with unit column stride")
+            dims[i] = Dims(f.shape[1], f.shape[0], f.stride(0))
+            fptr[i] = f.data_ptr()
+        dev = frames[0].device
+        outs = [[torch.empty((num_cells(d.w, d.h, cell), 4), dtype=torch.int32, device=dev) for d in dims]
+                for _ in range(npar)]
+        counts = torch.empty((npar, n), dtype=torch.int32, device=dev)
+        optr = (ctypes.c_void_p * (npar * n))(*[o.data_ptr() for row in outs for o in row])
+        th = (ctypes.c_int * npar)(*[p[0] for p in params])
+        ar = (ctypes.c_int * npar)(*[p[1] for p in params])
+        self._check(self.lib.vio_detect_sweep(self.ctx, fptr, dims, n, th, ar, npar, cell, levels, optr,
+                                              ctypes.c_void_p(counts.data_ptr()), _stream_handle(stream)))
+        return outs, counts
+
+    def detect_sweep_ptrs(self, fptr, dims, n, th, ar, npar, cell, levels, optr, counts_ptr, stream_handle):
+        """Pre-marshalled sweep call (ctypes arrays), for timing loops."""
+        self._check(self.lib.vio_detect_sweep(self.ctx, fptr, dims, n, th, ar, npar, cell, levels, optr, counts_ptr,
+                                              stream_handle))
 
     def detect_ptrs(self, fptr, dims, n, thresh, arc_len, cell, levels, optr, counts_ptr, stream_handle):
         """Pre-marshalled call (ctypes arrays), for timing loops."""

@@ -75,6 +75,29 @@ def test_mixed_batch_64_frames(dets, mixed, cell):
     assert_parity(got, cnt, mixed, 15, 9, cell, 3, 0)
 
 
+SWEEP = [(t, a) for a in (12, 9) for t in (5, 10, 20, 40)]
+
+
+def test_large_frames_sweep_pyramid_once(dets):
+    """3840x2160, 4 levels, 64x64 cells, the 8 (thresh, arc) settings in one
+    sweep call (pyramid built once): every setting equals a plain vio_detect
+    call; frame 0 is checked against the oracle for all settings, frame 1 for
+    one."""
+    imgs = [synth.make_frame(3840, 2160, seed=100 + i, n_shapes=400) for i in range(2)]
+    frames = [to_gpu(im) for im in imgs]
+    outs, counts = dets[0].detect_sweep(frames, SWEEP, 64, 4)
+    dets[0].sync()
+    cnt = counts.cpu().numpy()
+    for p, (thresh, arc) in enumerate(SWEEP):
+        got = [o.cpu().numpy() for o in outs[p]]
+        ref, ref_cnt = run(dets[0], imgs, thresh, arc, 64, 4)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), (thresh, arc)
+        assert np.array_equal(cnt[p], ref_cnt)
+        check = imgs if (thresh, arc) == (10, 9) else imgs[:1]
+        assert_parity(got, cnt[p], check, thresh, arc, 64, 4, 0)
+
+
 def test_large_frames_sampled(dets):
     """3840x2160, 4 levels, 64x64 cells: two frames of the 32-frame set in
     one launch, all eight (arc, thresh) combinations checked on frame 0 and
