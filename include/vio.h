@@ -87,6 +87,9 @@ typedef struct {
     int autotune;            /* 1 = time tile shapes on the first call of a shape    */
     int use_graphs;          /* 1 = replay each batch shape as a captured CUDA graph */
     int profile;             /* 1 = record CUDA events around each stage (vio_stage_ms) */
+    int nms_radius;          /* 1..4: non-maximum suppression keeps a pixel whose score
+                                is >= every score of its (2r+1) x (2r+1) neighbourhood
+                                (Section I-B; Table III compares r = 1..4)           */
 } vio_config;
 
 /* One frame: width, height, row pitch in bytes (pitch >= w). */
@@ -100,8 +103,12 @@ typedef struct {
 } vio_feature;
 
 /* Fills *cfg with the defaults: device 0, no budget, 64 frames, SAD-B,
- * autotune off, graphs on, profiling off. */
+ * autotune off, graphs on, profiling off, 3 x 3 NMS (radius 1). */
 void vio_config_default(vio_config* cfg);
+
+/* Copies the configuration the context was created with into *out.
+ * Errors: VIO_ERR_INVALID_ARG for NULL pointers. */
+vio_status vio_get_config(const vio_ctx* ctx, vio_config* out);
 
 /* Creates a context on cfg->device.  *out receives the context or NULL.
  * Errors: VIO_ERR_INVALID_ARG (NULL pointers, ranges), VIO_ERR_UNSUPPORTED
@@ -188,12 +195,15 @@ vio_status vio_sync(vio_ctx* ctx, vio_stream stream);
 
 /*
  * Tile configuration of the fused kernel.  tile_w x tile_h level pixels per
- * work item, cta_per_sm resident CTAs per SM for the persistent launch.
- * vio_get_tuning reports the configuration in use; vio_set_tuning pins one
- * (VIO_ERR_INVALID_ARG if it is not one of the built variants).
+ * work item, cta_per_sm resident CTAs per SM for the persistent launch,
+ * nms_radius the NMS window the variant was built for.  vio_get_tuning
+ * reports the configuration in use; vio_set_tuning pins one
+ * (VIO_ERR_INVALID_ARG if it is not one of the built variants or was built
+ * for another NMS radius than the context's).  The autotuner only times the
+ * variants of the context's radius.
  */
 typedef struct {
-    int tile_w, tile_h, cta_per_sm, variant;
+    int tile_w, tile_h, cta_per_sm, variant, nms_radius;
 } vio_tuning;
 
 vio_status vio_get_tuning(const vio_ctx* ctx, vio_tuning* out);

@@ -28,19 +28,29 @@ using DetectFn = void (*)(const uint8_t*, int32_t*, uint32_t*);
 using PyrFn = void (*)(const uint8_t*);
 
 struct Variant {
-    int tw, th, smem;
+    int tw, th, radius, smem;
     DetectFn fn[3];
 };
 
-template <int TH>
+template <int TH, int R>
 Variant make_variant() {
-    return Variant{TileGeom<TH>::TW, TH, TileGeom<TH>::SMEM,
-                   {fast_nms_cell_kernel<TH, 0>, fast_nms_cell_kernel<TH, 1>, fast_nms_cell_kernel<TH, 2>}};
+    return Variant{TileGeom<TH, R>::TW, TH, R, TileGeom<TH, R>::SMEM,
+                   {fast_nms_cell_kernel<TH, 0, R>, fast_nms_cell_kernel<TH, 1, R>, fast_nms_cell_kernel<TH, 2, R>}};
 }
 
+// 3x3 NMS in three tile heights; the wider windows of radius R keep the
+// score region at 64 rows.
 const std::vector<Variant>& variants() {
-    static const std::vector<Variant> v = {make_variant<62>(), make_variant<30>(), make_variant<126>()};
+    static const std::vector<Variant> v = {make_variant<62, 1>(), make_variant<30, 1>(), make_variant<126, 1>(),
+                                           make_variant<60, 2>(), make_variant<58, 3>(), make_variant<56, 4>()};
     return v;
+}
+
+// first variant built for NMS radius r (the default tile shape of that radius)
+int first_variant(int r) {
+    for (int i = 0; i < (int)variants().size(); ++i)
+        if (variants()[i].radius == r) return i;
+    return -1;
 }
 
 PyrFn pyr_fn(int levels) {
@@ -53,7 +63,7 @@ PyrFn pyr_fn(int levels) {
     }
 }
 
-constexpr int kBoxW = 144;  // TMA box width of every variant
+constexpr int kBoxW = 144;  // TMA box width of every variant (height: th + 2 radius + 6)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -401,12 +411,13 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
         f.out = outs[i];
         f.lev[0] = const_cast<uint8_t*>(lev0[i]);
         f.pitch[0] = pitch0[i];
-        if ((st = encode_map(ctx, &maps0[i], lev0[i], f.w, f.h, pitch0[i], kBoxW, v.th + 8)) != VIO_OK) return st;
+        if ((st = encode_map(ctx, &maps0[i], lev0[i], f.w, f.h, pitch0[i], kBoxW, v.th + 2 * v.radius + 6)) != VIO_OK)
+            return st;
         for (int k = 1; k < levels; ++k) {
             f.lev[k] = ctx->d_pyr + lev_off[i][k];
             f.pitch[k] = lev_pitch[i][k];
             if ((st = encode_map(ctx, &mapsk[(size_t)i * (kMaxLevels - 1) + k - 1], f.lev[k], f.w >> k, f.h >> k,
-                                 f.pitch[k], kBoxW, v.th + 8)) != VIO_OK)
+                                 f.pitch[k], kBoxW, v.th + 2 * v.radius + 6)) != VIO_OK)
                 return st;
         }
     }
@@ -447,9 +458,10 @@ vio_status autotune(vio_ctx* ctx, const ShapeKey& key, const uint8_t* const* lev
     VIO_CK(cudaEventCreate(&e0));
     VIO_CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_v = 0;
+    int best_v = first_variant(ctx->cfg.nms_radius);
     vio_status st = VIO_OK;
     for (int vi = 0; vi < (int)variants().size() && st == VIO_OK; ++vi) {
+        if (variants()[vi].radius != ctx->cfg.nms_radius) continue;
         for (int r = 0; r < 2 && st == VIO_OK; ++r)
             st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
         if (st != VIO_OK) break;
@@ -477,7 +489,7 @@ vio_status detect_impl(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitc
                        cudaStream_t s) {
     int vi = ctx->pinned_variant;
     if (vi < 0) {
-        vi = 0;
+        vi = first_variant(ctx->cfg.nms_radius);
         if (ctx->cfg.autotune) {
             const ShapeKey key = shape_key(dims, n, cell, levels);
             auto it = ctx->tuned.find(key);
@@ -510,6 +522,13 @@ void vio_config_default(vio_config* cfg) {
     cfg->autotune = 0;
     cfg->use_graphs = 1;
     cfg->profile = 0;
+    cfg->nms_radius = 1;
+}
+
+vio_status vio_get_config(const vio_ctx* ctx, vio_config* out) {
+    if (!ctx || !out) return VIO_ERR_INVALID_ARG;
+    *out = ctx->cfg;
+    return VIO_OK;
 }
 
 const char* vio_status_str(vio_status s) {
@@ -541,6 +560,7 @@ vio_status vio_variant(int i, vio_tuning* out) {
     out->tile_h = variants()[i].th;
     out->cta_per_sm = 0;
     out->variant = i;
+    out->nms_radius = variants()[i].radius;
     return VIO_OK;
 }
 
@@ -549,7 +569,8 @@ vio_status vio_create(vio_ctx** out, const vio_config* cfg_in) {
     *out = nullptr;
     vio_config cfg;
     if (cfg_in) cfg = *cfg_in; else vio_config_default(&cfg);
-    if (cfg.max_frames < 1 || cfg.max_frames > 1024 || cfg.score < 0 || cfg.score > 2 || cfg.device < 0)
+    if (cfg.max_frames < 1 || cfg.max_frames > 1024 || cfg.score < 0 || cfg.score > 2 || cfg.device < 0 ||
+        first_variant(cfg.nms_radius) < 0)
         return VIO_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device >= ndev) return VIO_ERR_CUDA;
@@ -701,7 +722,7 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
                 pitch0[i] = p;
             }
     }
-    int vi = ctx->pinned_variant >= 0 ? ctx->pinned_variant : 0;
+    int vi = ctx->pinned_variant >= 0 ? ctx->pinned_variant : first_variant(ctx->cfg.nms_radius);
     if (ctx->pinned_variant < 0 && ctx->cfg.autotune) {
         const ShapeKey key = shape_key(dims, n, cell, levels);
         if (!ctx->tuned.count(key)) {
@@ -817,6 +838,8 @@ vio_status vio_set_tuning(vio_ctx* ctx, const vio_tuning* t) {
     }
     if (t->variant < 0 || t->variant >= (int)variants().size())
         return fail(ctx, VIO_ERR_INVALID_ARG, "unknown variant");
+    if (variants()[t->variant].radius != ctx->cfg.nms_radius)
+        return fail(ctx, VIO_ERR_INVALID_ARG, "variant was built for another NMS radius");
     ctx->pinned_variant = t->variant;
     return VIO_OK;
 }

@@ -335,10 +335,11 @@ __device__ __forceinline__ uint32_t coarse4(uint32_t C, uint32_t L, uint32_t R, 
 // ---------------------------------------------------------------------------
 // Fused detect: persistent CTAs pull (frame, level, tile) items from a
 // counter.  A tile is 120 x TH level pixels; its "score region" adds a ring
-// (4 px left and right, 1 row up and down) so that it is exactly 128 pixels
-// wide: 16 lanes of 8 pixels cover a row, a warp covers a pair of rows.
+// (4 px left and right, R rows up and down for an NMS radius R) so that it is
+// exactly 128 pixels wide: 16 lanes of 8 pixels cover a row, a warp covers a
+// pair of rows.
 // Per item:
-//   1. TMA loads the region plus the 3-pixel circle halo (box 144 x TH+8)
+//   1. TMA loads the region plus the 3-pixel circle halo (box 144 x TH+2R+6)
 //      into one of two image buffers; the other buffer is loading the next
 //      item meanwhile.
 //   2. Coarse test on every score-region pixel, 8 pixels per lane, pixels
@@ -347,18 +348,20 @@ __device__ __forceinline__ uint32_t coarse4(uint32_t C, uint32_t L, uint32_t R, 
 //   3. Each warp runs the full segment test and score on its queue, writes
 //      scores into the score tile and compacts the corners in place.
 //   4. After a barrier of the consumer warps (NMS reads other warps' rows),
-//      3x3 NMS on the corner lists; when a warp's survivors share one cell
+//      (2R+1)x(2R+1) NMS on the corner lists; when a warp's survivors share one cell
 //      their packed keys are max-reduced with __reduce_max_sync and folded
 //      into the global cell key with one atomicMax, otherwise each survivor
 //      does its own atomicMax.
 // ---------------------------------------------------------------------------
-template <int TH>
+constexpr int kTileW = 120;  // output pixels per tile row, every variant
+
+template <int TH, int R = 1>
 struct TileGeom {
-    static constexpr int TW = 120;         // output pixels per tile row
+    static constexpr int TW = kTileW;      // output pixels per tile row
     static constexpr int SW = 128;         // score-region width (x0-4 .. x0+124)
-    static constexpr int SR = TH + 2;      // score-region rows (y0-1 .. y0+TH+1)
+    static constexpr int SR = TH + 2 * R;  // score-region rows (y0-R .. y0+TH+R): NMS radius R
     static constexpr int BW = 144;         // TMA box width (16-byte multiple)
-    static constexpr int BH = TH + 8;      // box rows y0-4 .. y0+TH+4
+    static constexpr int BH = SR + 6;      // box rows y0-R-3 .. y0+TH+R+3
     static constexpr int BOX = BW * BH;
     static constexpr int BOXA = (BOX + 127) / 128 * 128;
     static constexpr int WARPS = 8;
@@ -371,6 +374,7 @@ struct TileGeom {
     static constexpr int SMEM = Q_OFF + WARPS * QCAP * 2 + 128;  // +128: base alignment slack
     static_assert(SR % (2 * WARPS) == 0, "row pairs must split evenly over the warps");
     static_assert(BH <= 256, "TMA box limit");
+    static_assert(R >= 1 && R <= 4, "the 4-pixel column ring holds NMS radii up to 4");
 };
 
 constexpr int kConsumers = 256;             // 8 warps that detect
@@ -390,7 +394,6 @@ struct ItemInfo {
     uint64_t* keys;
 };
 
-template <int TH>
 __device__ __forceinline__ Item decode_item(const CallView& cv, const int32_t* tiles, int it) {
     const int n = cv.h->n_frames, L = cv.h->levels;
     const int j = upper_index(tiles, n * L, it);
@@ -399,7 +402,7 @@ __device__ __forceinline__ Item decode_item(const CallView& cv, const int32_t* t
     r.level = L - 1 - j / n;
     const int t = it - tiles[j];
     const int wk = cv.fds[r.frame].w >> r.level;
-    const int ntx = (wk + TileGeom<TH>::TW - 1) / TileGeom<TH>::TW;
+    const int ntx = (wk + kTileW - 1) / kTileW;
     r.ty = t / ntx;
     r.tx = t - r.ty * ntx;
     return r;
@@ -415,11 +418,11 @@ __device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x002
 // row pairs gather in one 32-bit word per lane (bit 8i + j = pair i, pixel j),
 // one warp scan of the popcounts places each lane's run in the queue, and
 // each lane writes its pixels by walking its set bits.
-template <bool HIGH_T, bool THREE, int TH>
+template <bool HIGH_T, bool THREE, int TH, int R>
 __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* queue, int xw, uint32_t k7,
                                                   int warp, int lane, int row_lo, int row_hi, uint32_t vm0,
                                                   uint32_t vm1) {
-    using G = TileGeom<TH>;
+    using G = TileGeom<TH, R>;
     constexpr int RW = G::BW / 4;
     constexpr int NW = (G::PPW + 3) / 4;  // mask words per lane
     const int half = lane >> 4, g = lane & 15;
@@ -433,9 +436,9 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
         const int r = 2 * p + half;
         if (r >= row_lo && r < row_hi) {
             const uint32_t* w = reinterpret_cast<const uint32_t*>(img + (3 + r) * G::BW) + xw + 2 * g;
-            const uint32_t L = w[-1], C0 = w[0], C1 = w[1], R = w[2];
+            const uint32_t L = w[-1], C0 = w[0], C1 = w[1], Rt = w[2];
             const uint32_t k0 = coarse4<HIGH_T, THREE>(C0, L, C1, w[-3 * RW], w[3 * RW], k7) & vm0;
-            const uint32_t k1 = coarse4<HIGH_T, THREE>(C1, C0, R, w[1 - 3 * RW], w[1 + 3 * RW], k7) & vm1;
+            const uint32_t k1 = coarse4<HIGH_T, THREE>(C1, C0, Rt, w[1 - 3 * RW], w[1 + 3 * RW], k7) & vm1;
             m[i >> 2] |= (nibble(k0) | (nibble(k1) << 4)) << (8 * (i & 3));
         }
     }
@@ -463,11 +466,11 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
     return __shfl_sync(0xFFFFFFFFu, incl, 31);
 }
 
-template <int TH, int MODE>
+template <int TH, int MODE, int R = 1>
 __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_t* __restrict__ call,
                                                                  int32_t* __restrict__ counter,
                                                                  uint32_t* __restrict__ status) {
-    using G = TileGeom<TH>;
+    using G = TileGeom<TH, R>;
     constexpr int NB = G::NBUF;
     extern __shared__ __align__(128) uint8_t smem_raw[];
     __shared__ uint64_t full_bar[NB], empty_bar[NB];
@@ -520,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
                     mbar_arrive(&full_bar[b]);
                     break;
                 }
-                const Item wi = decode_item<TH>(cv, tiles, it);
+                const Item wi = decode_item(cv, tiles, it);
                 const FrameDesc& fd = cv.fds[wi.frame];
                 in.level = wi.level;
                 in.x0 = wi.tx * G::TW;
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
                     wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
                 fence_tensormap_acquire(map);
                 mbar_arrive_expect_tx(&full_bar[b], G::BOX);
-                tma_load_2d(smem + G::IMG_OFF + b * G::BOXA, map, &full_bar[b], (in.x0 - 8) & ~15, in.y0 - 4);
+                tma_load_2d(smem + G::IMG_OFF + b * G::BOXA, map, &full_bar[b], (in.x0 - 8) & ~15, in.y0 - R - 3);
             }
         }
         return;
@@ -564,11 +567,12 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
         // 2. coarse test + compaction.  Testable pixels: 3 <= x < Wk-3, 3 <= y < Hk-3.
         int total;
         {
-            const int row_lo = max(0, 4 - y0), row_hi = min(G::SR, Hk - 2 - y0);
-            // NMS needs scores of score columns 3..124 (x0-1 .. x0+120) only
+            // score row r is level y = y0 - R + r; score column c is level x = x0 - 4 + c
+            const int row_lo = max(0, 3 - y0 + R), row_hi = min(G::SR, Hk - 3 - y0 + R);
+            // NMS needs scores of score columns 4-R .. 123+R (x0-R .. x0+119+R) only
             const int sx = 8 * (lane & 15);           // score column of this lane's first pixel
             const int lx = x0 - 4 + sx;               // its level x
-            const int xlo = max(3, 3 - x0 + 4), xhi = min(125, Wk - 3 - x0 + 4);  // kept score columns [xlo, xhi)
+            const int xlo = max(4 - R, 7 - x0), xhi = min(124 + R, Wk + 1 - x0);  // kept score columns [xlo, xhi)
             uint32_t vm0 = 0, vm1 = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -578,11 +582,11 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             (void)lx;
             const int xw = xoff / 4;
             if (high_t) {
-                total = three ? coarse_and_compact<true, true, TH>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1)
-                              : coarse_and_compact<true, false, TH>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1);
+                total = three ? coarse_and_compact<true, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1)
+                              : coarse_and_compact<true, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1);
             } else {
-                total = three ? coarse_and_compact<false, true, TH>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1)
-                              : coarse_and_compact<false, false, TH>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1);
+                total = three ? coarse_and_compact<false, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1)
+                              : coarse_and_compact<false, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1);
             }
         }
         __syncwarp();
@@ -626,14 +630,21 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             if (e < ncorner) {
                 const int idx = queue[e];
                 const int sr = idx >> 7, scx = idx & 127;
-                const bool inside = scx >= 4 && scx < 4 + G::TW && sr >= 1 && sr <= TH;
+                const bool inside = scx >= 4 && scx < 4 + G::TW && sr >= R && sr < R + TH;
                 if (inside) {
+                    // (2R+1) x (2R+1) neighbourhood: keep when >= every neighbour
                     const uint16_t* q = sc + idx;
                     const uint32_t s = q[0];
-                    const bool keep = s >= q[-G::SW - 1] && s >= q[-G::SW] && s >= q[-G::SW + 1] && s >= q[-1] &&
-                                      s >= q[1] && s >= q[G::SW - 1] && s >= q[G::SW] && s >= q[G::SW + 1];
+                    bool keep = true;
+                    // rows one at a time beyond 3x3: a whole 9x9 window of loads in
+                    // flight would spill under the 4-CTA register budget
+#pragma unroll(R == 1 ? 3 : 1)
+                    for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+                        for (int dx = -R; dx <= R; ++dx)
+                            if (dy != 0 || dx != 0) keep &= s >= q[dy * G::SW + dx];
                     if (keep) {
-                        const uint32_t x = (uint32_t)(x0 - 4 + scx), y = (uint32_t)(y0 - 1 + sr);
+                        const uint32_t x = (uint32_t)(x0 - 4 + scx), y = (uint32_t)(y0 - R + sr);
                         cell_id = __umulhi(y, magic) * (uint32_t)in.gw + __umulhi(x, magic);
                         hi = s;
                         lo = 0xFFFFFFFFu - (((uint32_t)k << 28) | (y * (uint32_t)Wk + x));

@@ -295,8 +295,12 @@ vio_status vio_serve_start(vio_ctx* ctx, const vio_serve_config* cfg) {
         cfg->queue_capacity < 1 || cfg->thresh < 0 || cfg->thresh > 255 || cfg->arc_len < 9 || cfg->arc_len > 16 ||
         cfg->cell_size < 32 || cfg->cell_size % 32 || cfg->levels < 1 || cfg->levels > VIO_MAX_LEVELS)
         return VIO_ERR_INVALID_ARG;
+    // lanes score and suppress like the parent context
     vio_config base;
-    vio_config_default(&base);
+    if (vio_get_config(ctx, &base) != VIO_OK) return VIO_ERR_INVALID_ARG;
+    base.mem_budget_bytes = 0;
+    base.autotune = 0;
+    base.profile = 0;
     const int dev = vio_device(ctx);
     if (dev < 0 || cudaSetDevice(dev) != cudaSuccess) return VIO_ERR_CUDA;
     auto* S = new vio_server_state();

@@ -31,7 +31,8 @@ class VioError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
                 ("max_frames", ctypes.c_int), ("score", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("use_graphs", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("use_graphs", ctypes.c_int), ("profile", ctypes.c_int),
+                ("nms_radius", ctypes.c_int)]
 
 
 class Dims(ctypes.Structure):
@@ -54,7 +55,7 @@ class ServeStats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
-                ("cta_per_sm", ctypes.c_int), ("variant", ctypes.c_int)]
+                ("cta_per_sm", ctypes.c_int), ("variant", ctypes.c_int), ("nms_radius", ctypes.c_int)]
 
 
 _lib = None
@@ -116,6 +117,8 @@ def load(build_if_missing: bool = True):
     lib.vio_set_tuning.restype = st
     lib.vio_device.argtypes = [P]
     lib.vio_device.restype = ci
+    lib.vio_get_config.argtypes = [P, ctypes.POINTER(Config)]
+    lib.vio_get_config.restype = st
     lib.vio_serve_config_default.argtypes = [ctypes.POINTER(ServeConfig)]
     lib.vio_serve_config_default.restype = None
     lib.vio_serve_start.argtypes = [P, ctypes.POINTER(ServeConfig)]
@@ -144,14 +147,20 @@ def num_cells(w: int, h: int, cell: int) -> int:
     return int(load().vio_num_cells(w, h, cell))
 
 
-def variants() -> list[tuple[int, int]]:
+def variants() -> list[tuple[int, int, int]]:
+    """(tile_w, tile_h, nms_radius) of every built variant, by variant index."""
     lib = load()
     out = []
     for i in range(lib.vio_num_variants()):
         t = Tuning()
         lib.vio_variant(i, ctypes.byref(t))
-        out.append((t.tile_w, t.tile_h))
+        out.append((t.tile_w, t.tile_h, t.nms_radius))
     return out
+
+
+def variant_ids(nms_radius: int = 1) -> list[int]:
+    """Indices of the variants built for one NMS radius."""
+    return [i for i, v in enumerate(variants()) if v[2] == nms_radius]
 
 
 def _stream_handle(stream) -> ctypes.c_void_p:
@@ -168,7 +177,7 @@ class Detector:
 
     def __init__(self, device: int = 0, max_frames: int = 64, score: int = SCORE_SAD_B,
                  mem_budget_bytes: int = 0, autotune: bool = False, use_graphs: bool = True,
-                 profile: bool = False):
+                 profile: bool = False, nms_radius: int = 1):
         self.lib = load()
         cfg = Config()
         self.lib.vio_config_default(ctypes.byref(cfg))
@@ -179,6 +188,7 @@ class Detector:
         cfg.autotune = int(autotune)
         cfg.use_graphs = int(use_graphs)
         cfg.profile = int(profile)
+        cfg.nms_radius = nms_radius
         self.cfg = cfg
         self.ctx = ctypes.c_void_p()
         s = self.lib.vio_create(ctypes.byref(self.ctx), ctypes.byref(cfg))
@@ -342,8 +352,13 @@ class Detector:
         if variant is None:
             self._check(self.lib.vio_set_tuning(self.ctx, None))
             return
-        t = Tuning(0, 0, 0, variant)
+        t = Tuning(0, 0, 0, variant, 0)
         self._check(self.lib.vio_set_tuning(self.ctx, ctypes.byref(t)))
+
+    def config(self) -> Config:
+        c = Config()
+        self._check(self.lib.vio_get_config(self.ctx, ctypes.byref(c)))
+        return c
 
     def tuning(self) -> tuple[int, int, int]:
         t = Tuning()

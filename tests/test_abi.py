@@ -40,15 +40,21 @@ def test_config_default(lib):
     cfg = vio.Config()
     lib.vio_config_default(ctypes.byref(cfg))
     assert (cfg.device, cfg.max_frames, cfg.score, cfg.autotune, cfg.use_graphs) == (0, 64, 0, 0, 1)
+    assert cfg.nms_radius == 1
 
 
 def test_variants_listed(lib):
     vs = vio.variants()
     assert len(vs) >= 3
-    for tw, th in vs:
+    for tw, th, r in vs:
         # a score region of tw + 8 = 128 pixels (one warp of 4-pixel words per
-        # row) and th + 2 rows split over 8 warps in groups of 4
-        assert tw + 8 == 128 and (th + 2) % 32 == 0 and th + 8 <= 256
+        # row) and th + 2r rows split over 8 warps in groups of 4; the TMA box
+        # adds the 3-row circle halo above and below
+        assert 1 <= r <= 4
+        assert tw + 8 == 128 and (th + 2 * r) % 32 == 0 and th + 2 * r + 6 <= 256
+    # every NMS radius of Table III has a variant, the 3x3 one first
+    assert vs[0][2] == 1 and sorted({r for _, _, r in vs}) == [1, 2, 3, 4]
+    assert vio.variant_ids(1)[0] == 0 and len(vio.variant_ids(1)) >= 3
     t = vio.Tuning()
     assert lib.vio_variant(len(vs), ctypes.byref(t)) == 1
 
@@ -61,6 +67,12 @@ def test_create_rejects_bad_config_and_null(lib):
     ctx = ctypes.c_void_p()
     assert lib.vio_create(ctypes.byref(ctx), ctypes.byref(cfg)) == 1
     assert not ctx
+    for r in (0, 5, -1):
+        lib.vio_config_default(ctypes.byref(cfg))
+        cfg.nms_radius = r
+        assert lib.vio_create(ctypes.byref(ctx), ctypes.byref(cfg)) == 1
+        assert not ctx
+    assert lib.vio_get_config(None, ctypes.byref(cfg)) == 1
 
 
 def test_destroy_null_is_noop(lib):

@@ -37,9 +37,9 @@ def run(det, imgs, thresh, arc, cell, levels, **kw):
     return [o.cpu().numpy() for o in outs], counts.cpu().numpy()
 
 
-def assert_parity(got, counts, imgs, thresh, arc, cell, levels, mode):
+def assert_parity(got, counts, imgs, thresh, arc, cell, levels, mode, nms_radius=1):
     for i, img in enumerate(imgs):
-        want, n = oracle.detect(img, thresh, arc, cell, levels, mode)
+        want, n = oracle.detect(img, thresh, arc, cell, levels, mode, nms_radius=nms_radius)
         if not np.array_equal(got[i], want):
             bad = np.nonzero((got[i] != want).any(axis=1))[0]
             raise AssertionError(f"frame {i} ({img.shape[1]}x{img.shape[0]}): {len(bad)} cells differ, "
@@ -166,7 +166,7 @@ def test_every_tile_variant_is_identical(dets, mixed):
     imgs = mixed[::8]
     ref, ref_cnt = run(dets[0], imgs, 15, 9, 32, 3)
     frames = [to_gpu(im) for im in imgs]
-    for v in range(len(vio.variants())):
+    for v in vio.variant_ids(1):
         dets[0].set_variant(v)
         outs, counts = dets[0].detect(frames, 15, 9, 32, 3)
         dets[0].sync()
@@ -256,12 +256,69 @@ def test_alternating_buffers_and_variants(dets):
     gb = [to_gpu(im) for im in b]
     want_a = [oracle.detect(im, 15, 9, 32, 3)[0] for im in a]
     want_b = [oracle.detect(im, 15, 9, 32, 3)[0] for im in b]
-    nv = len(vio.variants())
+    ids = vio.variant_ids(1)
+    nv = len(ids)
     for rep in range(3 * nv):
-        dets[0].set_variant(rep % nv if rep >= nv else None)
+        dets[0].set_variant(ids[rep % nv] if rep >= nv else None)
         imgs, want = (ga, want_a) if rep % 2 == 0 else (gb, want_b)
         outs, _ = dets[0].detect(imgs, 15, 9, 32, 3)
         dets[0].sync()
         for o, w in zip(outs, want):
             assert np.array_equal(o.cpu().numpy(), w), rep
     dets[0].set_variant(None)
+
+
+# ---- NMS windows of radius 2..4 (Section I-B, Table III) -----------------------
+
+@pytest.fixture(scope="module")
+def wide():
+    out = {r: vio.Detector(device=0, max_frames=64, nms_radius=r) for r in (2, 3, 4)}
+    yield out
+    for d in out.values():
+        d.close()
+
+
+@pytest.mark.parametrize("radius", [2, 3, 4])
+def test_wide_nms_mixed_batch(wide, mixed, radius):
+    imgs = mixed[::4]
+    got, cnt = run(wide[radius], imgs, 15, 9, 32, 3)
+    assert_parity(got, cnt, imgs, 15, 9, 32, 3, 0, nms_radius=radius)
+    # a wider window never keeps more cells than the 3x3 one finds features in
+    want3 = [oracle.detect(im, 15, 9, 32, 3)[1] for im in imgs]
+    assert all(c <= w for c, w in zip(cnt, want3))
+
+
+@pytest.mark.parametrize("radius", [2, 4])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_wide_nms_other_scores(mode, radius):
+    det = vio.Detector(max_frames=4, score=mode, nms_radius=radius)
+    img = synth.make_frame(752, 480, seed=31)
+    got, cnt = run(det, [img], 12, 9, 32, 3)
+    assert_parity(got, cnt, [img], 12, 9, 32, 3, mode, nms_radius=radius)
+    det.close()
+
+
+@pytest.mark.parametrize("radius", [2, 3, 4])
+def test_wide_nms_ragged_and_tile_edges(wide, radius):
+    # heights around multiples of the tile height (64 - 2r rows) and widths
+    # around the 120-pixel tile width, so the window straddles tile seams
+    th = 64 - 2 * radius
+    sizes = [(7, 7, 1), (31, 17, 1), (121, th + 1, 2), (239, 2 * th - 1, 2), (241, 3 * th, 3), (257, 131, 3)]
+    imgs = [synth.make_frame(w, h, seed=900 + i, n_shapes=12) for i, (w, h, _) in enumerate(sizes)]
+    for img, (_, _, levels) in zip(imgs, sizes):
+        got, cnt = run(wide[radius], [img], 8, 9, 32, levels)
+        assert_parity(got, cnt, [img], 8, 9, 32, levels, 0, nms_radius=radius)
+
+
+def test_wide_nms_autotune_and_tuning(mixed):
+    imgs = mixed[::8]
+    det = vio.Detector(max_frames=64, nms_radius=3, autotune=True)
+    got, cnt = run(det, imgs, 15, 9, 64, 3)
+    assert_parity(got, cnt, imgs, 15, 9, 64, 3, 0, nms_radius=3)
+    assert det.config().nms_radius == 3
+    tw, th, v = det.tuning()
+    assert v in vio.variant_ids(3) and th + 6 == 64
+    # a variant built for another radius is refused
+    with pytest.raises(vio.VioError):
+        det.set_variant(vio.variant_ids(1)[0])
+    det.close()

@@ -109,3 +109,20 @@ def test_serving_errors():
         det.poll(t, 64, 64)  # already taken
     det.serve_stop()
     det.close()
+
+
+def test_lanes_inherit_score_and_nms_radius(pool):
+    """Serving lanes score and suppress like the context that started them."""
+    det = vio.Detector(max_frames=16, score=vio.SCORE_MT, nms_radius=2)
+    det.serve_start(max_batch=4, lanes=2, **PARAMS)
+    picks = pool[::3]
+    tickets = [(det.submit(sid, f), f) for sid, f in picks]
+    det.drain(60000)
+    for t, f in tickets:
+        done, cells, cnt = det.poll(t, f.shape[1], f.shape[0])
+        assert done
+        ref, n = oracle.detect(f, PARAMS["thresh"], PARAMS["arc_len"], PARAMS["cell_size"], PARAMS["levels"],
+                               oracle.MT, nms_radius=2)
+        assert np.array_equal(cells, ref) and cnt == n
+    det.serve_stop()
+    det.close()
