@@ -140,3 +140,48 @@ def mixed_batch(first_seed: int = 2, per_size: int = 16, n_shapes: int = 40):
             frames.append(make_frame(w, h, seed, n_shapes))
             seed += 1
     return frames
+
+
+# ---- frame pairs for the feature tracker ------------------------------------
+#
+# A pair is a previous frame and a next frame that shows the same scene moved
+# by (dx, dy) pixels and with its intensities mapped by v -> gain * v + offset.
+# The scene is a sum of seeded plane waves (smooth, textured everywhere, no
+# flat areas), evaluated in float64 and rounded to 8 bits, so that sub-pixel
+# motion has an exact ground truth.  Unlike make_frame the bytes may differ in
+# the last bit between hosts (libm), which does not matter: the tracker and
+# its oracle always read the bytes generated on the same host.
+
+def _waves(seed: int, n: int = 6):
+    d = splitmix64(seed ^ 0x5A5A5A5A, 4 * n)
+    u = (d >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    freq = 0.05 + 0.25 * u[0::4]
+    ang = 2.0 * np.pi * u[1::4]
+    phase = 2.0 * np.pi * u[2::4]
+    amp = 12.0 + 16.0 * u[3::4]
+    return freq * np.cos(ang), freq * np.sin(ang), phase, amp
+
+
+def smooth_frame(w: int, h: int, seed: int, dx: float = 0.0, dy: float = 0.0, gain: float = 1.0,
+                 offset: float = 0.0) -> np.ndarray:
+    """The scene of `seed` moved by (dx, dy): pixel (x, y) shows scene point
+    (x - dx, y - dy); intensities gain * v + offset, rounded and clamped."""
+    kx, ky, phase, amp = _waves(seed)
+    y, x = np.mgrid[0:h, 0:w].astype(np.float64)
+    x -= dx
+    y -= dy
+    v = np.full((h, w), 128.0)
+    for i in range(len(kx)):
+        v += amp[i] * np.sin(kx[i] * x + ky[i] * y + phase[i]) * (0.8 if i % 2 else 1.0)
+    v = gain * v + offset
+    return np.ascontiguousarray(np.clip(np.floor(v + 0.5), 0, 255).astype(np.uint8))
+
+
+def shift_frame(img: np.ndarray, dx: int, dy: int, fill: int = 0) -> np.ndarray:
+    """img moved by whole pixels: out[y, x] = img[y - dy, x - dx]."""
+    h, w = img.shape
+    out = np.full_like(img, fill)
+    ys, yd = (slice(0, h - dy), slice(dy, h)) if dy >= 0 else (slice(-dy, h), slice(0, h + dy))
+    xs, xd = (slice(0, w - dx), slice(dx, w)) if dx >= 0 else (slice(-dx, w), slice(0, w + dx))
+    out[yd, xd] = img[ys, xs]
+    return out
