@@ -310,6 +310,75 @@ vio_status vio_serve_stop(vio_ctx* ctx);
 vio_status vio_detect_noalloc(const uint8_t* frame, vio_dims dims, int thresh, int arc_len, int cell_size,
                               int levels, int score, vio_feature* out_cells, int32_t* out_count, vio_stream stream);
 
+/*
+ * Feature tracker (Section II-E, Eqs. 2-6): the pyramidal approximated
+ * simultaneous inverse compositional Lucas-Kanade tracker.  For each feature
+ * at a level-0 position (x, y) of a previous frame it estimates the
+ * translation t = (t_x, t_y) and the affine intensity change (alpha, beta)
+ * such that  next(p + t) ~ (1 + alpha) prev(p) + beta  over a square patch
+ * around the feature, coarse to fine over a pyramid built like the
+ * detector's (Section II-B).  Per level: the template patch and its
+ * central-difference gradients are sampled once (bilinear), the Hessian
+ * H = sum U U^T with U = [(1+alpha) dT/dx, (1+alpha) dT/dy, T, 1] (Eq. 4) is
+ * formed once with the appearance at the start of the level, and each
+ * iteration solves dq = H^-1 sum U r, r = next(p + t) - (1+alpha) T - beta
+ * (Eq. 6), then t -= dt, alpha += d_alpha, beta += d_beta.  One warp tracks
+ * one feature (Section II-E) and sums over the patch with a butterfly of
+ * warp shuffles.  Arithmetic is fp32.
+ *
+ * Readings: a level-0 position x is (x + 0.5) / 2^k - 0.5 on level k; the
+ * patch is P x P samples at offsets i - (P - 1) / 2; bilinear samples need
+ * 0 <= x <= W_k - 2 and 0 <= y <= H_k - 2, and a sample outside it, or a
+ * Hessian that is not positive definite, loses the track; the translation
+ * doubles from one level to the next finer one.
+ */
+enum { VIO_TRACK_GAIN = 1, VIO_TRACK_OFFSET = 2 };
+
+typedef struct {
+    int levels;        /* 1..VIO_MAX_LEVELS; the smallest level must be >= 7 x 7          */
+    int patch_fine;    /* patch side on level 0: 8 or 16                                    */
+    int patch_coarse;  /* patch side on levels >= 1: 8 or 16                                */
+    int max_iters;     /* iterations per level, 1..100                                      */
+    float min_update;  /* a level ends when |dt| < min_update (pixels of that level); >= 0  */
+    int model;         /* VIO_TRACK_GAIN | VIO_TRACK_OFFSET bits: parameters estimated      */
+} vio_track_params;
+
+/* One tracked feature (32 bytes). */
+typedef struct {
+    float x, y;          /* level-0 position in the next frame                         */
+    float gain, offset;  /* alpha, beta                                                 */
+    int32_t status;      /* 1 = tracked, 0 = lost                                       */
+    int32_t iters;       /* iterations over all levels                                  */
+    float residual;      /* RMS of the residual in the last iteration on level 0        */
+    int32_t reserved;
+} vio_track_result;
+
+/* Fills *p with the defaults: 3 levels, 16 x 16 on level 0, 8 x 8 above,
+ * 30 iterations, min_update 0.01, gain and offset estimated. */
+void vio_track_params_default(vio_track_params* p);
+
+/*
+ * Tracks n_pts[i] features from prev[i] to next[i] for i < n_pairs, one
+ * launch for all pairs.
+ *
+ *   prev, next  host arrays of n_pairs DEVICE pointers to uint8 frames; pair
+ *               i has both frames of size dims[i] (pitch dims[i].pitch).
+ *               Frames whose address or pitch is not a multiple of 16 are
+ *               first copied into a context slot.
+ *   pts         host array of n_pairs DEVICE pointers to float[2 * n_pts[i]]
+ *               level-0 positions (x, y) in prev[i]
+ *   n_pts       host int[n_pairs], each >= 0
+ *   params      NULL for the defaults
+ *   out         host array of n_pairs DEVICE pointers, pair i receiving
+ *               n_pts[i] records
+ *
+ * Asynchronous on `stream`.  Errors: VIO_ERR_INVALID_ARG (NULL pointers,
+ * ranges, frames smaller than the pyramid allows), VIO_ERR_OOM, VIO_ERR_CUDA.
+ */
+vio_status vio_track(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* const* next, const vio_dims* dims,
+                     int n_pairs, const float* const* pts, const int* n_pts, const vio_track_params* params,
+                     vio_track_result* const* out, vio_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

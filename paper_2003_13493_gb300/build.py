@@ -52,16 +52,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(" ".join(cmd))
         subprocess.check_call(cmd)
 
-    with ThreadPoolExecutor(max(1, len(objs))) as ex:
-        list(ex.map(compile_one, zip(_sources(), objs)))
     tmp = LIB_PATH + f".tmp{pid}"
-    link = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
-    if verbose:
-        print(" ".join(link))
-    subprocess.check_call(link)
-    for o in objs:
-        os.remove(o)
-    os.replace(tmp, LIB_PATH)
+    try:
+        with ThreadPoolExecutor(max(1, len(objs))) as ex:
+            list(ex.map(compile_one, zip(_sources(), objs)))
+        link = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
+        if verbose:
+            print(" ".join(link))
+        subprocess.check_call(link)
+        os.replace(tmp, LIB_PATH)
+    finally:
+        for o in objs + [tmp]:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB_PATH
 
 

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/vio.h"
+#include "vio_ctx.h"
 #include "vio_kernels.cuh"
 
 using namespace vio;
@@ -65,12 +66,6 @@ PyrFn pyr_fn(int levels) {
 
 constexpr int kBoxW = 144;  // TMA box width of every variant (height: th + 2 radius + 6)
 
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 // Bytes of the largest call block a context can send.
 size_t call_block_cap(int max_frames) {
     size_t b = align_up(sizeof(CallHeader), 128);
@@ -83,130 +78,9 @@ size_t call_block_cap(int max_frames) {
     return b;
 }
 
-struct ShapeKey {
-    std::vector<int32_t> v;
-    bool operator==(const ShapeKey& o) const { return v == o.v; }
-};
-struct ShapeHash {
-    size_t operator()(const ShapeKey& k) const {
-        size_t h = 1469598103934665603ull;
-        for (int32_t x : k.v) h = (h ^ (uint32_t)x) * 1099511628211ull;
-        return h;
-    }
-};
-
-struct MapKey {
-    uintptr_t ptr;
-    int32_t w, h, pitch, bw, bh;
-    bool operator==(const MapKey& o) const {
-        return ptr == o.ptr && w == o.w && h == o.h && pitch == o.pitch && bw == o.bw && bh == o.bh;
-    }
-};
-struct MapHash {
-    size_t operator()(const MapKey& k) const {
-        return std::hash<uintptr_t>()(k.ptr) ^ ((size_t)k.w * 73856093u) ^ ((size_t)k.h * 19349663u) ^
-               ((size_t)k.pitch * 83492791u) ^ ((size_t)k.bw << 40) ^ ((size_t)k.bh << 52);
-    }
-};
-
 }  // namespace
 
-// ---------------------------------------------------------------------------
-// Context
-// ---------------------------------------------------------------------------
-struct vio_ctx {
-    vio_config cfg{};
-    int sm_count = 0;
-    std::string err;
-    EncodeTiledFn encode = nullptr;
-    size_t call_cap = 0;
-
-    // resident device buffers
-    uint8_t* d_call = nullptr;          // the current call block
-    int32_t* d_counter = nullptr;       // work-item counter of the fused kernel
-    uint64_t* d_keys = nullptr;         // packed cell keys, zero when idle
-    size_t keys_cap = 0;
-    uint8_t* d_pyr = nullptr;           // pyramid levels 1..L-1 of every frame
-    size_t pyr_cap = 0;
-    uint8_t* d_in = nullptr;            // staged level-0 frames (host path / unaligned frames)
-    size_t in_cap = 0;
-    int4* d_cells = nullptr;            // host path: device-side output records + counts
-    size_t cells_cap = 0;
-    size_t bytes_in_use = 0;
-
-    // host
-    uint32_t* h_status = nullptr;       // pinned, device-mapped status word
-    uint32_t* d_status = nullptr;
-    uint8_t* h_stage = nullptr;         // pinned ring of call blocks
-    int ring = 8, ring_pos = 0;
-    std::vector<cudaEvent_t> ring_ev;
-    uint8_t* h_out = nullptr;           // pinned host-path output staging
-    size_t h_out_cap = 0;
-
-    cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaStream_t capture_stream = nullptr;
-    cudaEvent_t last_ev = nullptr;
-    cudaStream_t last_stream = nullptr;
-    bool have_last = false;
-
-    // one graph per (variant, levels): every batch shape replays it
-    cudaGraphExec_t graphs[8][kMaxLevels + 1] = {};
-    int grid_fused[8] = {};
-    std::unordered_map<ShapeKey, int, ShapeHash> tuned;  // batch shape -> variant
-    std::unordered_map<MapKey, CUtensorMap, MapHash> map_cache;
-    int pinned_variant = -1;
-    int last_variant = 0;
-
-    void drop_graphs() {
-        for (auto& row : graphs)
-            for (auto& g : row)
-                if (g) {
-                    cudaGraphExecDestroy(g);
-                    g = nullptr;
-                }
-    }
-};
-
 namespace {
-
-vio_status fail(vio_ctx* c, vio_status s, const std::string& msg) {
-    if (c) c->err = msg;
-    return s;
-}
-
-#define VIO_CK(call)                                                                          \
-    do {                                                                                      \
-        cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess) {                                                              \
-            return fail(ctx, e_ == cudaErrorMemoryAllocation ? VIO_ERR_OOM : VIO_ERR_CUDA,    \
-                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
-        }                                                                                     \
-    } while (0)
-
-// Grows a resident buffer to `need` bytes.  Growing waits for the device
-// (the old buffer may still be in use), so buffers grow geometrically.
-vio_status grow(vio_ctx* ctx, void** p, size_t* cap, size_t need, bool zero) {
-    if (need <= *cap && *p) return VIO_OK;
-    size_t want = std::max(need, *cap + *cap / 2);
-    const size_t budget = ctx->cfg.mem_budget_bytes;
-    if (budget && ctx->bytes_in_use - *cap + want > budget) {
-        want = need;
-        if (ctx->bytes_in_use - *cap + want > budget)
-            return fail(ctx, VIO_ERR_OOM, "context memory budget exceeded");
-    }
-    if (*p) {
-        VIO_CK(cudaDeviceSynchronize());
-        VIO_CK(cudaFree(*p));
-        ctx->bytes_in_use -= *cap;
-        *p = nullptr;
-        *cap = 0;
-    }
-    VIO_CK(cudaMalloc(p, want));
-    if (zero) VIO_CK(cudaMemset(*p, 0, want));
-    *cap = want;
-    ctx->bytes_in_use += want;
-    return VIO_OK;
-}
 
 vio_status encode_map(vio_ctx* ctx, CUtensorMap* out, const void* ptr, int w, int h, int pitch, int bw, int bh) {
     MapKey key{(uintptr_t)ptr, w, h, pitch, bw, bh};
@@ -626,6 +500,7 @@ vio_status vio_destroy(vio_ctx* ctx) {
     cudaSetDevice(ctx->cfg.device);
     cudaDeviceSynchronize();
     ctx->drop_graphs();
+    track_release(ctx);
     cudaFree(ctx->d_call);
     cudaFree(ctx->d_counter);
     cudaFree(ctx->d_keys);

@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
 // clears the key for the next call and counts non-empty cells per frame
 // (warp-aggregated; the fused kernel zeroed the counts).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) decode_kernel(const uint8_t* __restrict__ call, int32_t* __restrict__ counter) {
+static __global__ void __launch_bounds__(256) decode_kernel(const uint8_t* __restrict__ call, int32_t* __restrict__ counter) {
     const CallView cv(call);
     const int nf = cv.h->n_frames, total = cv.h->n_cells;
     int32_t* counts = cv.h->counts;

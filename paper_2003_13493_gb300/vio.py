@@ -53,6 +53,15 @@ class ServeStats(ctypes.Structure):
                 ("frames_per_s", ctypes.c_double)]
 
 
+class TrackParams(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("patch_fine", ctypes.c_int), ("patch_coarse", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("min_update", ctypes.c_float), ("model", ctypes.c_int)]
+
+
+TRACK_GAIN, TRACK_OFFSET = 1, 2
+TRACK_RESULT_WORDS = 8  # x, y, gain, offset (float) | status, iters (int32) | residual (float) | reserved
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
                 ("cta_per_sm", ctypes.c_int), ("variant", ctypes.c_int), ("nms_radius", ctypes.c_int)]
@@ -119,6 +128,11 @@ def load(build_if_missing: bool = True):
     lib.vio_device.restype = ci
     lib.vio_get_config.argtypes = [P, ctypes.POINTER(Config)]
     lib.vio_get_config.restype = st
+    lib.vio_track_params_default.argtypes = [ctypes.POINTER(TrackParams)]
+    lib.vio_track_params_default.restype = None
+    lib.vio_track.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(Dims), ci, ctypes.POINTER(P),
+                              ctypes.POINTER(ci), ctypes.POINTER(TrackParams), ctypes.POINTER(P), P]
+    lib.vio_track.restype = st
     lib.vio_serve_config_default.argtypes = [ctypes.POINTER(ServeConfig)]
     lib.vio_serve_config_default.restype = None
     lib.vio_serve_start.argtypes = [P, ctypes.POINTER(ServeConfig)]
@@ -156,6 +170,16 @@ def variants() -> list[tuple[int, int, int]]:
         lib.vio_variant(i, ctypes.byref(t))
         out.append((t.tile_w, t.tile_h, t.nms_radius))
     return out
+
+
+def track_fields(res):
+    """Splits (n, 8) float32 tracker records (numpy) into
+    (xy float32 (n, 2), gain, offset, status int32, iters int32, residual)."""
+    import numpy as np
+
+    r = np.ascontiguousarray(res, dtype=np.float32)
+    ints = r.view(np.int32)
+    return r[:, 0:2], r[:, 2], r[:, 3], ints[:, 4], ints[:, 5], r[:, 6]
 
 
 def variant_ids(nms_radius: int = 1) -> list[int]:
@@ -233,6 +257,47 @@ class Detector:
         self._check(self.lib.vio_detect(self.ctx, fptr, dims, n, thresh, arc_len, cell, levels, optr,
                                         ctypes.c_void_p(counts.data_ptr()), _stream_handle(stream)))
         return outs, counts
+
+    def track(self, prev, nxt, pts, params: dict | None = None, outs=None, stream=None):
+        """Feature tracking (Section II-E) of pts[i] from prev[i] to nxt[i].
+
+        prev, nxt: lists of 2-D uint8 CUDA tensors (same size per pair);
+        pts: list of (n_i, 2) float32 CUDA tensors of level-0 (x, y);
+        params: overrides of vio_track_params fields.  Returns a list of
+        (n_i, 8) float32 CUDA tensors in the vio_track_result layout (use
+        track_fields to split them)."""
+        import torch
+
+        n = len(prev)
+        if len(nxt) != n or len(pts) != n:
+            raise ValueError("prev, nxt and pts must have one entry per pair")
+        dims = (Dims * n)()
+        pp = (ctypes.c_void_p * n)()
+        nn = (ctypes.c_void_p * n)()
+        for i, (a, b) in enumerate(zip(prev, nxt)):
+            for f in (a, b):
+                if f.dtype != torch.uint8 or f.dim() != 2 or f.stride(1) != 1 or not f.is_cuda:
+                    raise ValueError("frames must be 2-D uint8 CUDA tensors with unit column stride")
+            if a.shape != b.shape or a.stride(0) != b.stride(0):
+                raise ValueError("both frames of a pair need the same size and pitch")
+            dims[i] = Dims(a.shape[1], a.shape[0], a.stride(0))
+            pp[i] = a.data_ptr()
+            nn[i] = b.data_ptr()
+        for q in pts:
+            if q.dtype != torch.float32 or q.dim() != 2 or q.shape[1] != 2 or not q.is_contiguous():
+                raise ValueError("pts must be contiguous (n, 2) float32 tensors")
+        if outs is None:
+            outs = [torch.empty((q.shape[0], TRACK_RESULT_WORDS), dtype=torch.float32, device=q.device) for q in pts]
+        tp = TrackParams()
+        self.lib.vio_track_params_default(ctypes.byref(tp))
+        for k, v in (params or {}).items():
+            setattr(tp, k, v)
+        qp = (ctypes.c_void_p * n)(*[q.data_ptr() for q in pts])
+        cnt = (ctypes.c_int * n)(*[q.shape[0] for q in pts])
+        op = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        self._check(self.lib.vio_track(self.ctx, pp, nn, dims, n, qp, cnt, ctypes.byref(tp), op,
+                                       _stream_handle(stream)))
+        return outs
 
     def detect_sweep(self, frames, params, cell: int, levels: int, stream=None):
         """params: list of (thresh, arc_len).  Returns (outs[p][i] tensors, counts (n_params, n))."""

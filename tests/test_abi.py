@@ -77,3 +77,11 @@ def test_create_rejects_bad_config_and_null(lib):
 
 def test_destroy_null_is_noop(lib):
     assert lib.vio_destroy(None) == 0
+
+
+def test_track_defaults_and_null_context(lib):
+    p = vio.TrackParams()
+    lib.vio_track_params_default(ctypes.byref(p))
+    assert (p.levels, p.patch_fine, p.patch_coarse, p.max_iters, p.model) == (3, 16, 8, 30, 3)
+    assert abs(p.min_update - 0.01) < 1e-7
+    assert lib.vio_track(None, None, None, None, 0, None, None, None, None, None) == 1
