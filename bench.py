@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/profile legs")
     ap.add_argument("--spin", type=float, default=0.5, help="seconds of untimed steps before timing")
     ap.add_argument("--variant", type=int, default=-1, help="pin a tile variant instead of autotuning")
+    ap.add_argument("--no-tracker", action="store_true", help="skip the feature-tracker leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson serving run (0 skips it)")
     return ap.parse_args()
@@ -391,6 +392,51 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     if sweep:
         return out
 
+    # the other scores of Section II-D on the same batches (same tile variant)
+    scores = {}
+    for name, mode in (("sad_a", vio.SCORE_SAD_A), ("mt", vio.SCORE_MT)):
+        d = vio.Detector(device=dev.index, max_frames=max(64, n), score=mode)
+        d.set_variant(det.tuning()[2])
+        ssteps = max(5, min(args.steps, 200))
+        for i in range(3):
+            fp, dd = marshalled[i % len(marshalled)]
+            d.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], optr, cptr, sh)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(ssteps):
+            fp, dd = marshalled[i % len(marshalled)]
+            d.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], optr, cptr, sh)
+        e1.record(stream)
+        d.sync(stream)
+        sms = e0.elapsed_time(e1) / ssteps
+        d.close()
+        scores[name] = {"value": round(n / (sms / 1e3), 1), "unit": "frames/s", "ms_per_step": round(sms, 5)}
+    out["scores"] = scores
+
+    # Table III's windows: 3x3 .. 9x9 NMS, on the same batches at 1 level, FAST-10, thresh 10
+    wins = {}
+    for r in (1, 2, 3, 4):
+        d = vio.Detector(device=dev.index, max_frames=max(64, n), nms_radius=r)
+        wsteps = max(5, min(args.steps, 200))
+        for i in range(3):
+            fp, dd = marshalled[i % len(marshalled)]
+            d.detect_ptrs(fp, dd, n, 10, 10, 32, 1, optr, cptr, sh)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(wsteps):
+            fp, dd = marshalled[i % len(marshalled)]
+            d.detect_ptrs(fp, dd, n, 10, 10, 32, 1, optr, cptr, sh)
+        e1.record(stream)
+        d.sync(stream)
+        wms = e0.elapsed_time(e1) / wsteps
+        d.close()
+        wins[f"{2 * r + 1}x{2 * r + 1}"] = {"value": round(n / (wms / 1e3), 1), "unit": "frames/s",
+                                            "ms_per_step": round(wms, 5)}
+    out["nms_windows"] = {"what": "the batch at 1 level, FAST-10, thresh 10, 32x32 cells (Table III's setting)",
+                          **wins}
+
     # plain path: one frame per call
     plain = vio.Detector(device=dev.index, max_frames=4)
     plain.set_variant(det.tuning()[2])
@@ -440,11 +486,97 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
 
     if args.serve_seconds > 0:
         out["serving"] = serving_leg(args, dev.index)
+    if not args.no_tracker:
+        out["tracker"] = tracker_leg(args, dev.index)
 
     if not args.no_cpu_baseline:
         rate, cores, sample = oracle_rate(frames_np, wl, args.cpu_seconds)
         out["cpu_baseline"] = {"value": round(rate, 2), "unit": "frames/s", "cores": cores, "kind": "oracle",
                                "sample": sample}
+    return out
+
+
+def tracker_leg(args, dev_index: int) -> dict:
+    """Feature tracker (Section II-E): throughput of one vio_track call over
+    64 pairs of 752x480 frames x 256 features (a 16 x 16 grid inside a 40-pixel
+    margin), and the latency of one pair with 100 features for each model of
+    Table VI (both pyramids built inside the call).  Frames: the smooth
+    moving scene of synth.smooth_frame with seeded sub-pixel motion and
+    intensity change; default parameters (3 levels, 16 x 16 / 8 x 8 patches,
+    30 iterations, min_update 0.01)."""
+    import numpy as np
+    import torch
+
+    from oracle import lk_oracle as lk
+    from paper_2003_13493_gb300 import synth, vio
+
+    rng = np.random.default_rng(9)
+    w, h, npairs = 752, 480, 64
+    ys, xs = np.meshgrid(np.linspace(40, h - 40, 16), np.linspace(40, w - 40, 16), indexing="ij")
+    grid = np.stack([xs.ravel(), ys.ravel()], axis=1).astype(np.float32)
+    pairs = []
+    for i in range(npairs):
+        dx, dy = rng.uniform(-4, 4, 2)
+        g, o = rng.uniform(0.9, 1.1), rng.uniform(-10, 10)
+        pairs.append((synth.smooth_frame(w, h, seed=300 + i),
+                      synth.smooth_frame(w, h, seed=300 + i, dx=dx, dy=dy, gain=g, offset=o)))
+    dev = torch.device("cuda", dev_index)
+    prev = [torch.from_numpy(a).to(dev) for a, _ in pairs]
+    nxt = [torch.from_numpy(b).to(dev) for _, b in pairs]
+    pts = [torch.from_numpy(grid).to(dev) for _ in pairs]
+    det = vio.Detector(device=dev_index, max_frames=npairs)
+    outs = det.track(prev, nxt, pts)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        det.track(prev, nxt, pts, outs=outs)
+    reps = max(5, min(args.steps, 50))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        det.track(prev, nxt, pts, outs=outs)
+    e1.record(stream)
+    det.sync()
+    ms = e0.elapsed_time(e1) / reps
+    res = np.concatenate([o.cpu().numpy() for o in outs])
+    _, _, _, status, iters, _ = vio.track_fields(res)
+    out = {"value": round(npairs * len(grid) / (ms / 1e3), 1), "unit": "features/s",
+           "ms_per_call": round(ms, 4), "features_per_call": npairs * len(grid),
+           "tracked_frac": round(float((status == 1).mean()), 4), "mean_iters": round(float(iters.mean()), 2),
+           "what": "one vio_track call: 64 pairs of 752x480 x 256 features, pyramids of both frames included"}
+    # Table VI: 100 features on one pair, per model
+    p100 = [torch.from_numpy(grid[::256 // 100][:100].copy()).to(dev)]
+    lat = {}
+    for name, model in (("trans", 0), ("trans_offset", vio.TRACK_OFFSET), ("trans_gain", vio.TRACK_GAIN),
+                        ("trans_gain_offset", vio.TRACK_GAIN | vio.TRACK_OFFSET)):
+        o1 = det.track(prev[:1], nxt[:1], p100, dict(model=model))
+        for _ in range(5):
+            det.track(prev[:1], nxt[:1], p100, dict(model=model), outs=o1)
+        det.sync()
+        e0.record(stream)
+        for _ in range(reps):
+            det.track(prev[:1], nxt[:1], p100, dict(model=model), outs=o1)
+        e1.record(stream)
+        det.sync()
+        lat[name] = round(e0.elapsed_time(e1) / reps * 1e3, 1)
+    out["latency_us_100_features"] = lat
+    out["paper_ms_100_features"] = {"tegra_x2": {"trans": 0.96, "trans_offset": 0.90, "trans_gain": 0.91,
+                                                 "trans_gain_offset": 1.01},
+                                    "gtx_960m": {"trans": 0.33, "trans_offset": 0.28, "trans_gain": 0.29,
+                                                 "trans_gain_offset": 0.38}}
+    det.close()
+    if not args.no_cpu_baseline:
+        # the oracle on a bounded sample: the first 64 features of the first pairs
+        t0 = time.perf_counter()
+        done = 0
+        for a, b in pairs:
+            lk.track(a, b, grid[:64].astype(np.float64), levels=3)
+            done += 64
+            if time.perf_counter() - t0 > min(5.0, args.cpu_seconds):
+                break
+        out["cpu_baseline"] = {"value": round(done / (time.perf_counter() - t0), 1), "unit": "features/s",
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"{done} features of the same pairs, fp64 numpy, one thread"}
     return out
 
 
