@@ -654,8 +654,12 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
     std::vector<const uint8_t*> lev0(n);
     std::vector<int4*> outs(n);
     for (int i = 0; i < n; ++i) {
-        VIO_CK(cudaMemcpy2DAsync(ctx->d_in + off[i], pitch0[i], host_frames[i], dims[i].pitch, dims[i].w, dims[i].h,
-                                 cudaMemcpyHostToDevice, s));
+        if (dims[i].pitch == pitch0[i])  // rows already 16-byte multiples: one contiguous copy
+            VIO_CK(cudaMemcpyAsync(ctx->d_in + off[i], host_frames[i], (size_t)pitch0[i] * dims[i].h,
+                                   cudaMemcpyHostToDevice, s));
+        else
+            VIO_CK(cudaMemcpy2DAsync(ctx->d_in + off[i], pitch0[i], host_frames[i], dims[i].pitch, dims[i].w,
+                                     dims[i].h, cudaMemcpyHostToDevice, s));
         lev0[i] = ctx->d_in + off[i];
         outs[i] = ctx->d_cells + coff[i];
     }

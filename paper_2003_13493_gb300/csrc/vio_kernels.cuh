@@ -209,6 +209,66 @@ __device__ __forceinline__ uint32_t pack4(uint32_t a, uint32_t b, uint32_t c, ui
     return __byte_perm(__byte_perm(a, b, 0x0040), __byte_perm(c, d, 0x0040), 0x5410);
 }
 
+// 16-bit-lane minimum and maximum on the DPX unit.
+__device__ __forceinline__ uint32_t min16x2(uint32_t a, uint32_t b) { return __vimin3_u16x2(a, b, b); }
+
+// Window minima of length 8 + R over the 16 cyclic differences held two per
+// word (word j = elements 2j, 2j+1), from the windows of 8 in M8.
+template <int R>
+__device__ __forceinline__ uint32_t mt_best(const uint32_t (&M8)[8]) {
+    uint32_t W[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        // elements 2j + R, 2j + R + 1
+        const uint32_t S = (R & 1) ? __byte_perm(M8[(j + R / 2) & 7], M8[(j + R / 2 + 1) & 7], 0x5432)
+                                   : M8[(j + R / 2) & 7];
+        W[j] = min16x2(M8[j], S);
+    }
+    uint32_t b = __vimax3_u16x2(W[0], W[1], W[2]);
+    b = __vimax3_u16x2(b, W[3], W[4]);
+    b = __vimax3_u16x2(b, W[5], W[6]);
+    b = __vimax3_u16x2(b, W[7], W[7]);
+    return max(b & 0xFFFFu, b >> 16);
+}
+
+// MT score (Section II-D) of a corner with circle values v, centre c and arc
+// polarity `bright`.  Raising the threshold only removes points from the
+// masks, so a window of n points that fails at the detection threshold t
+// holds a difference <= t while a passing window has all differences > t:
+// the largest minimum over all 16 windows is a passing window's and equals
+// MT + 1.  Differences (v - c for a bright arc, c - v for a dark one) are
+// biased by 256 into 16-bit lanes, two circle points per word (no borrow
+// crosses a lane: every biased value is in 1..511), and the window minima
+// are built by doubling: 2, 4, 8, then 8 + r as two overlapping windows of 8.
+__device__ __forceinline__ uint32_t mt_score(const uint32_t (&v)[16], uint32_t c, bool bright, int n) {
+    const uint32_t c2 = c * 0x00010001u;
+    uint32_t D[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t V = __byte_perm(v[2 * j], v[2 * j + 1], 0x5410);
+        D[j] = bright ? V + (0x01000100u - c2) : (0x01000100u + c2) - V;
+    }
+    uint32_t M2[8], M4[8], M8[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) M2[j] = min16x2(D[j], __byte_perm(D[j], D[(j + 1) & 7], 0x5432));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) M4[j] = min16x2(M2[j], M2[(j + 1) & 7]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) M8[j] = min16x2(M4[j], M4[(j + 2) & 7]);
+    uint32_t best;
+    switch (n) {  // uniform over the launch
+        case 9: best = mt_best<1>(M8); break;
+        case 10: best = mt_best<2>(M8); break;
+        case 11: best = mt_best<3>(M8); break;
+        case 12: best = mt_best<4>(M8); break;
+        case 13: best = mt_best<5>(M8); break;
+        case 14: best = mt_best<6>(M8); break;
+        case 15: best = mt_best<7>(M8); break;
+        default: best = mt_best<8>(M8); break;
+    }
+    return best - 257u;  // remove the bias and the final -1
+}
+
 // Full segment test and score of the pixel at shared-memory pointer p in a
 // tile of row pitch P (compile time).  Returns 0 when it is not a corner.
 //
@@ -255,29 +315,19 @@ __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, i
         d |= rotl16(d, 2);
         d |= rotl16(d, 4);  // windows of 8 starting at each start
         const uint32_t run = d | rotl16(d, n - 8);
+        // SAD over the run: each nibble of the run mask spreads to a byte
+        // mask of its four circle points (bit i -> bit 8i by one multiply;
+        // the shifted copies occupy disjoint bits, so nothing carries)
+        const uint32_t c4 = c * 0x01010101u;
         uint32_t s = 0;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) s += ((run >> i) & 1u) ? (uint32_t)abs((int)v[i] - (int)c) : 0u;
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t m = (((run >> (4 * q)) & 0xFu) * 0x00204081u & 0x01010101u) * 0xFFu;
+            s += __vsadu4(pack4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]) & m, c4 & m);
+        }
         return s;
     } else {  // MT: largest window minimum of the arc's polarity, minus 1
-        // Raising the threshold only removes points from the masks, so only
-        // windows that pass at `t` can pass above it; their minimum
-        // difference d (strictly above the threshold) gives MT = d - 1.
-        int dp[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) dp[i] = bright ? (int)v[i] - (int)c : (int)c - (int)v[i];
-        int best = 0;
-#pragma unroll
-        for (int s0 = 0; s0 < 16; ++s0) {
-            if ((starts >> s0) & 1u) {
-                int mn = 255;
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (j < n) mn = min(mn, dp[(s0 + j) & 15]);
-                best = max(best, mn);
-            }
-        }
-        return (uint32_t)(best - 1);
+        return mt_score(v, c, bright, n);
     }
 }
 
@@ -600,22 +650,18 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             int idx = 0;
             if (e < total) {
                 idx = queue[e];
-                // box offset of score-region pixel (idx >> 7, idx & 127); SAD-B
-                // is scored below, on the corners only
-                s = eval_corner<MODE, G::BW, MODE != 0>(img_base + idx + 16 * (idx >> 7), thresh, n_arc);
+                // box offset of score-region pixel (idx >> 7, idx & 127); the
+                // score is taken below, on the compacted corners only
+                s = eval_corner<MODE, G::BW, false>(img_base + idx + 16 * (idx >> 7), thresh, n_arc);
             }
             const uint32_t cm = __ballot_sync(0xFFFFFFFFu, s != 0);
-            if (s) {
-                if (MODE != 0) sc[idx] = (uint16_t)s;
-                queue[ncorner + __popc(cm & lt_mask)] = (uint16_t)idx;
-            }
+            if (s) queue[ncorner + __popc(cm & lt_mask)] = (uint16_t)idx;
             ncorner += __popc(cm);
         }
-        if (MODE == 0) {
-            for (int e = lane; e < ncorner; e += 32) {
-                const int idx = queue[e];
-                sc[idx] = (uint16_t)sad_b<G::BW>(img_base + idx + 16 * (idx >> 7));
-            }
+        for (int e = lane; e < ncorner; e += 32) {
+            const int idx = queue[e];
+            const uint8_t* p = img_base + idx + 16 * (idx >> 7);
+            sc[idx] = (uint16_t)(MODE == 0 ? sad_b<G::BW>(p) : eval_corner<MODE, G::BW, true>(p, thresh, n_arc));
         }
         // this warp is done with the image buffer
         __syncwarp();
