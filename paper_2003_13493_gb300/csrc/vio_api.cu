@@ -82,6 +82,17 @@ size_t call_block_cap(int max_frames) {
 
 namespace {
 
+// Device address of pinned (page-locked, device-mapped) host memory, else
+// nullptr (pageable memory, device memory, or an unknown pointer).
+const void* device_alias(const void* host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();  // clear the error: an unknown pointer is not a failure here
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 vio_status encode_map(vio_ctx* ctx, CUtensorMap* out, const void* ptr, int w, int h, int pitch, int bw, int bh) {
     MapKey key{(uintptr_t)ptr, w, h, pitch, bw, bh};
     auto it = ctx->map_cache.find(key);
@@ -192,9 +203,17 @@ vio_status get_graph(vio_ctx* ctx, int variant, int levels, bool pyramid, cudaGr
 
 // Lays the batch out in the resident arenas, fills the call block, uploads
 // it and launches the three kernels on `s`.
+// Frames that the pyramid kernel uploads itself: src[i] non-null is the
+// device mapping of frame i in host memory (row pitch pitch[i]); lev0[i] is
+// then the device copy that kernel writes.
+struct Upload {
+    const uint8_t* const* src = nullptr;
+    const int* pitch = nullptr;
+};
+
 vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims,
                   int n, int thresh, int arc, int cell, int levels, int4* const* outs, int32_t* counts,
-                  cudaStream_t s, bool pyramid = true) {
+                  cudaStream_t s, bool pyramid = true, Upload up = {}) {
     const Variant& v = variants()[variant];
     // arena layout
     size_t koff = 0, poff = 0;
@@ -285,6 +304,10 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
         f.out = outs[i];
         f.lev[0] = const_cast<uint8_t*>(lev0[i]);
         f.pitch[0] = pitch0[i];
+        if (up.src && up.src[i]) {
+            f.src0 = up.src[i];
+            f.src0_pitch = up.pitch[i];
+        }
         if ((st = encode_map(ctx, &maps0[i], lev0[i], f.w, f.h, pitch0[i], kBoxW, v.th + 2 * v.radius + 6)) != VIO_OK)
             return st;
         for (int k = 1; k < levels; ++k) {
@@ -327,7 +350,7 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
 
 vio_status autotune(vio_ctx* ctx, const ShapeKey& key, const uint8_t* const* lev0, const int* pitch0,
                     const vio_dims* dims, int n, int thresh, int arc, int cell, int levels, int4* const* outs,
-                    int32_t* counts, cudaStream_t s) {
+                    int32_t* counts, cudaStream_t s, Upload up = {}) {
     cudaEvent_t e0, e1;
     VIO_CK(cudaEventCreate(&e0));
     VIO_CK(cudaEventCreate(&e1));
@@ -337,12 +360,12 @@ vio_status autotune(vio_ctx* ctx, const ShapeKey& key, const uint8_t* const* lev
     for (int vi = 0; vi < (int)variants().size() && st == VIO_OK; ++vi) {
         if (variants()[vi].radius != ctx->cfg.nms_radius) continue;
         for (int r = 0; r < 2 && st == VIO_OK; ++r)
-            st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
+            st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s, true, up);
         if (st != VIO_OK) break;
         VIO_CK(cudaEventRecord(e0, s));
         const int reps = 5;
         for (int r = 0; r < reps && st == VIO_OK; ++r)
-            st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
+            st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s, true, up);
         VIO_CK(cudaEventRecord(e1, s));
         VIO_CK(cudaEventSynchronize(e1));
         float ms = 0;
@@ -360,7 +383,7 @@ vio_status autotune(vio_ctx* ctx, const ShapeKey& key, const uint8_t* const* lev
 
 vio_status detect_impl(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims, int n,
                        int thresh, int arc, int cell, int levels, int4* const* outs, int32_t* counts,
-                       cudaStream_t s) {
+                       cudaStream_t s, Upload up = {}) {
     int vi = ctx->pinned_variant;
     if (vi < 0) {
         vi = first_variant(ctx->cfg.nms_radius);
@@ -368,7 +391,7 @@ vio_status detect_impl(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitc
             const ShapeKey key = shape_key(dims, n, cell, levels);
             auto it = ctx->tuned.find(key);
             if (it == ctx->tuned.end()) {
-                vio_status st = autotune(ctx, key, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
+                vio_status st = autotune(ctx, key, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s, up);
                 if (st != VIO_OK) return st;
                 it = ctx->tuned.find(key);
             }
@@ -376,7 +399,7 @@ vio_status detect_impl(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitc
         }
     }
     ctx->last_variant = vi;
-    return launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s);
+    return launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s, true, up);
 }
 
 }  // namespace
@@ -651,23 +674,50 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
         VIO_CK(cudaHostAlloc(&ctx->h_out, cell_bytes, cudaHostAllocDefault));
         ctx->h_out_cap = cell_bytes;
     }
-    std::vector<const uint8_t*> lev0(n);
+    // Frames in pinned host memory are read by the pyramid kernel through
+    // their device mapping (it writes the device copy of level 0 as it goes),
+    // so the upload overlaps the pyramid; records go straight into pinned
+    // output buffers.  Anything else takes the copy engines.
+    std::vector<const uint8_t*> lev0(n), src0(n, nullptr);
+    std::vector<int> src_pitch(n, 0);
     std::vector<int4*> outs(n);
+    std::vector<bool> direct_out(n, false);
+    bool any_up = false;
     for (int i = 0; i < n; ++i) {
-        if (dims[i].pitch == pitch0[i])  // rows already 16-byte multiples: one contiguous copy
+        lev0[i] = ctx->d_in + off[i];
+        const uint8_t* mapped = static_cast<const uint8_t*>(device_alias(host_frames[i]));
+        if (levels > 1 && mapped && ((uintptr_t)mapped & 15) == 0 && (dims[i].pitch & 15) == 0) {
+            src0[i] = mapped;
+            src_pitch[i] = dims[i].pitch;
+            any_up = true;
+        } else if (dims[i].pitch == pitch0[i]) {  // rows already 16-byte multiples: one contiguous copy
             VIO_CK(cudaMemcpyAsync(ctx->d_in + off[i], host_frames[i], (size_t)pitch0[i] * dims[i].h,
                                    cudaMemcpyHostToDevice, s));
-        else
+        } else {
             VIO_CK(cudaMemcpy2DAsync(ctx->d_in + off[i], pitch0[i], host_frames[i], dims[i].pitch, dims[i].w,
                                      dims[i].h, cudaMemcpyHostToDevice, s));
-        lev0[i] = ctx->d_in + off[i];
-        outs[i] = ctx->d_cells + coff[i];
+        }
+        int4* out_mapped = static_cast<int4*>(const_cast<void*>(device_alias(host_cells[i])));
+        direct_out[i] = out_mapped && ((uintptr_t)out_mapped & 15) == 0;
+        outs[i] = direct_out[i] ? out_mapped : ctx->d_cells + coff[i];
     }
     int32_t* d_counts = reinterpret_cast<int32_t*>(ctx->d_cells + ncell_total);
+    Upload up;
+    if (any_up) {
+        up.src = src0.data();
+        up.pitch = src_pitch.data();
+    }
     if ((st = detect_impl(ctx, lev0.data(), pitch0.data(), dims, n, thresh, arc, cell, levels, outs.data(),
-                          d_counts, s)) != VIO_OK)
+                          d_counts, s, up)) != VIO_OK)
         return st;
-    VIO_CK(cudaMemcpyAsync(ctx->h_out, ctx->d_cells, cell_bytes, cudaMemcpyDeviceToHost, s));
+    // records that did not go straight to the caller, then the counts
+    bool all_direct = true;
+    for (int i = 0; i < n; ++i) all_direct &= direct_out[i];
+    if (all_direct)
+        VIO_CK(cudaMemcpyAsync(ctx->h_out + ncell_total * sizeof(int4), d_counts, sizeof(int32_t) * n,
+                               cudaMemcpyDeviceToHost, s));
+    else
+        VIO_CK(cudaMemcpyAsync(ctx->h_out, ctx->d_cells, cell_bytes, cudaMemcpyDeviceToHost, s));
     VIO_CK(cudaStreamSynchronize(s));
     if (*ctx->h_status) {
         *ctx->h_status = 0;
@@ -675,7 +725,8 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
     }
     const int4* rec = reinterpret_cast<const int4*>(ctx->h_out);
     for (int i = 0; i < n; ++i)
-        std::memcpy(host_cells[i], rec + coff[i], vio_num_cells(dims[i].w, dims[i].h, cell) * sizeof(int4));
+        if (!direct_out[i])
+            std::memcpy(host_cells[i], rec + coff[i], vio_num_cells(dims[i].w, dims[i].h, cell) * sizeof(int4));
     if (host_counts)
         std::memcpy(host_counts, ctx->h_out + ncell_total * sizeof(int4), sizeof(int32_t) * n);
     return VIO_OK;

@@ -17,9 +17,11 @@ struct FrameDesc {
     int32_t w, h;          // level-0 size
     int32_t gw, gh;        // cell grid
     int32_t pyr_bx;        // pyramid thread blocks along x
-    int32_t pad0;
+    int32_t src0_pitch;    // row pitch of src0
     uint64_t* keys;        // gw * gh packed cell keys (0 = empty)
-    int4* out;             // gw * gh output records
+    int4* out;             // gw * gh output records (device or device-mapped host memory)
+    const uint8_t* src0;   // non-null: level 0 is read from here (device-mapped host
+                           // memory) by the pyramid kernel, which also writes it to lev[0]
     uint8_t* lev[kMaxLevels];   // level 0 is the caller's frame (read only)
     int32_t pitch[kMaxLevels];
     int32_t pad1[3];
@@ -104,8 +106,12 @@ __global__ void __launch_bounds__(256) pyramid_kernel(const uint8_t* __restrict_
         const int x0 = tx * 16, y0 = ty * B;
         if (x0 >= W || y0 >= H) continue;
         const int W1 = W >> 1, H1 = H >> 1;
-        const uint8_t* src = fd.lev[0];
-        const int sp = fd.pitch[0];
+        // level 0 comes from the frame itself or, when the frame sits in
+        // host memory, from its device mapping; then this kernel is also the
+        // upload and writes the rows it reads to the device copy of level 0
+        const bool upload = fd.src0 != nullptr;
+        const uint8_t* src = upload ? fd.src0 : fd.lev[0];
+        const int sp = upload ? fd.src0_pitch : fd.pitch[0];
         // level 0 rows; the last partial chunk of a row is read byte by byte
         uint4 r[B];
 #pragma unroll
@@ -114,11 +120,17 @@ __global__ void __launch_bounds__(256) pyramid_kernel(const uint8_t* __restrict_
             r[j] = make_uint4(0, 0, 0, 0);
             if (y < H) {
                 const uint8_t* p = src + (size_t)y * sp + x0;
+                uint8_t* d = fd.lev[0] + (size_t)y * fd.pitch[0] + x0;
                 if (x0 + 16 <= W) {
                     r[j] = *reinterpret_cast<const uint4*>(p);
+                    if (upload) *reinterpret_cast<uint4*>(d) = r[j];
                 } else {
                     uint32_t wv[4] = {0, 0, 0, 0};
-                    for (int i = 0; i < W - x0; ++i) wv[i >> 2] |= (uint32_t)p[i] << (8 * (i & 3));
+                    for (int i = 0; i < W - x0; ++i) {
+                        const uint8_t b = p[i];
+                        wv[i >> 2] |= (uint32_t)b << (8 * (i & 3));
+                        if (upload) d[i] = b;
+                    }
                     r[j] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
                 }
             }

@@ -210,6 +210,46 @@ def test_host_path_matches(dets, mixed):
     assert_parity(outs, counts, [mixed[16]], 15, 9, 32, 3, 0)
 
 
+def pinned_like(a, offset=0):
+    """A page-locked host copy of a (numpy view of pinned torch memory),
+    starting `offset` bytes into its buffer."""
+    buf = torch.empty(a.nbytes + offset + 64, dtype=torch.uint8).pin_memory()
+    v = buf.numpy()[offset:offset + a.nbytes].view(a.dtype).reshape(a.shape)
+    v[...] = a
+    return buf, v
+
+
+def test_host_path_pinned_buffers(dets, mixed):
+    """Pinned frames are read by the pyramid kernel through their device
+    mapping and pinned outputs are written in place; the results must not
+    change, alone or mixed with pageable and misaligned buffers."""
+    imgs = mixed[::6]
+    keep = []
+    frames = []
+    for i, im in enumerate(imgs):
+        if i % 3 == 0:
+            frames.append(im)                         # pageable: copy engine
+        else:
+            b, v = pinned_like(im, offset=0 if i % 3 == 1 else 1)  # aligned / misaligned pinned
+            keep.append(b)
+            frames.append(v)
+    outs = []
+    for i, im in enumerate(imgs):
+        shape = (vio.num_cells(im.shape[1], im.shape[0], 32), 4)
+        if i % 2:
+            b, v = pinned_like(np.full(shape, 7, np.int32))
+            keep.append(b)
+            outs.append(v)
+        else:
+            outs.append(np.full(shape, 7, np.int32))
+    for mode in (0, 2):
+        got, counts = dets[mode].detect_host(frames, 15, 9, 32, 3, outs=outs)
+        assert_parity(got, counts, imgs, 15, 9, 32, 3, mode)
+    # one level: no pyramid kernel, the pinned frames take the copy engine
+    got, counts = dets[0].detect_host(frames, 15, 9, 32, 1, outs=[np.empty_like(o) for o in outs])
+    assert_parity(got, counts, imgs, 15, 9, 32, 1, 0)
+
+
 def test_invalid_arguments_rejected(dets):
     img = to_gpu(synth.make_frame(64, 64, seed=1))
     d = dets[0]
