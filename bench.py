@@ -129,30 +129,36 @@ class ClockSampler:
 
 # ---- ncu traffic recorded for the current kernel source ------------------------
 
-def kernel_source_hash() -> str:
-    import glob
+KERNEL_SOURCES = {
+    "fast_nms_cell": ("ptx.cuh", "vio_kernels.cuh"),
+    "fast_sweep": ("ptx.cuh", "vio_kernels.cuh", "vio_sweep.cuh"),
+}
 
+
+def kernel_source_hash(kernel: str = "fast_nms_cell") -> str:
+    """Hash of the sources a detect kernel is compiled from."""
     h = hashlib.sha256()
-    for name in ("ptx.cuh", "vio_kernels.cuh"):  # the sources of the fused detect kernel
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2003_13493_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    """dram bytes per launch of the fused kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", f"fast_nms_cell_{workload}.md")
+def recorded_traffic(workload: str, kernel: str = "fast_nms_cell"):
+    """dram bytes per launch of a detect kernel from its committed ncu
+    summary (profiles/<kernel>_<workload>.md), if it was taken on the current
+    kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     src = traffic = None
     with open(path) as f:
         for line in f:
             if line.startswith("kernel_source_sha256:"):
-                src = line.split(":", 1)[1].strip()
+                src = line.split(":", 1)[1].split()[0].strip()
             if line.startswith("dram_bytes_per_launch:"):
                 traffic = float(line.split(":", 1)[1].strip())
-    return traffic if src == kernel_source_hash() else None
+    return traffic if src == kernel_source_hash(kernel) else None
 
 
 def max_over_ranks(value: float) -> float:
@@ -215,20 +221,21 @@ def oracle_rate(frames, wl, seconds: float):
 # ---- our implementation ------------------------------------------------------------
 
 def algorithmic_bytes(dims, levels, cell, num_cells, npar=1):
-    """Per-step bytes and the fused kernel's bytes per launch.
+    """Per-step bytes and the detect kernel's bytes per launch.
 
     A step reads level 0 once, writes and reads each pyramid level once and
-    writes 16 bytes per cell; with npar detections over the same pyramid each
-    further detection re-reads every level and writes its own cells.  The
-    fused kernel reads every level once and updates 8 bytes of key per cell."""
+    writes 16 bytes per cell.  A sweep of npar settings is one fused pass: the
+    levels are read once for all settings, each setting writes its own cells.
+    The detect kernel reads every level once and updates 8 bytes of key per
+    cell and setting."""
     step = 0.0
     fused = 0.0
     for (w, h) in dims:
         nc = num_cells(w, h, cell)
         pyr_px = sum((w >> k) * (h >> k) for k in range(1, levels))
         all_px = sum((w >> k) * (h >> k) for k in range(levels))
-        step += w * h + 2 * pyr_px + (npar - 1) * all_px + npar * 16 * nc
-        fused += all_px + 8 * nc
+        step += w * h + 2 * pyr_px + npar * 16 * nc
+        fused += all_px + 8 * nc * npar
     return step, fused
 
 
@@ -362,12 +369,20 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     acc = [0.0, 0.0, 0.0]
     sweep = wl.get("sweep")
     npar = len(sweep) if sweep else 1
+    if sweep:
+        th = (ctypes.c_int * npar)(*[p[0] for p in sweep])
+        ar = (ctypes.c_int * npar)(*[p[1] for p in sweep])
+        sw_optr = (ctypes.c_void_p * (npar * n))(*([optr[i] for i in range(n)] * npar))
+        sw_counts = torch.empty(npar * n, dtype=torch.int32, device=dev)
     for i in range(steps + 3):
         fp, dd = marshalled[i % len(marshalled)]
-        # one detection per step here (the first setting of a sweep): the
-        # stage events time each kernel of that launch
-        t0, a0 = (sweep[0] if sweep else (wl["thresh"], wl["arc"]))
-        prof.detect_ptrs(fp, dd, n, t0, a0, wl["cell"], wl["levels"], optr, cptr, sh)
+        # the stage events time each kernel of the step's (last) launch: for a
+        # sweep of at most 8 settings that is the one fused launch
+        if sweep:
+            prof.detect_sweep_ptrs(fp, dd, n, th, ar, npar, wl["cell"], wl["levels"], sw_optr,
+                                   ctypes.c_void_p(sw_counts.data_ptr()), sh)
+        else:
+            prof.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], optr, cptr, sh)
         st = prof.stage_ms()
         if i >= 3:
             acc = [a + b for a, b in zip(acc, st)]
@@ -377,12 +392,13 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     peaks, kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = fused_bytes / (stage[1] * 1e-3) / 1e9
-    traffic = recorded_traffic(args.workload)
+    kname = "fast_sweep_kernel" if sweep and npar <= 8 else "fast_nms_cell_kernel"
+    traffic = recorded_traffic(args.workload, kname.replace("_kernel", ""))
     out["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                        "frac": round(achieved / peak, 4), "traffic": traffic,
-                       "kernel": "fast_nms_cell_kernel", "peak_kind": f"{kind} hbm_gbs",
+                       "kernel": kname, "peak_kind": f"{kind} hbm_gbs",
                        "algorithmic_bytes_per_launch": int(fused_bytes)}
-    out["stage_ms"] = {"pyramid": round(stage[0], 5), "fast_nms_cell": round(stage[1], 5),
+    out["stage_ms"] = {"pyramid": round(stage[0], 5), kname.replace("_kernel", ""): round(stage[1], 5),
                        "decode": round(stage[2], 5)}
     step_gbs = step_bytes / (ms_per_step * 1e-3) / 1e9
     out["step_roofline"] = {"algorithmic_bytes_per_step": int(step_bytes), "achieved_gbs": round(step_gbs, 1),

@@ -17,6 +17,7 @@
 #include "../../include/vio.h"
 #include "vio_ctx.h"
 #include "vio_kernels.cuh"
+#include "vio_sweep.cuh"
 
 using namespace vio;
 
@@ -75,6 +76,9 @@ size_t call_block_cap(int max_frames) {
     b += align_up(sizeof(int32_t) * (max_frames * kMaxLevels + 1), 128);
     b += align_up(sizeof(int32_t) * (max_frames + 1), 128);
     b += align_up(sizeof(int32_t) * (max_frames + 1), 128);
+    // sweep section and its output table
+    b += align_up(sizeof(SweepInfo), 128);
+    b += align_up(sizeof(int4*) * kMaxSweep * max_frames, 128);
     return b;
 }
 
@@ -211,9 +215,47 @@ struct Upload {
     const int* pitch = nullptr;
 };
 
+// Up to kMaxSweep settings detected by one fused sweep launch (thresholds
+// non-decreasing); outs[s * n + i] receives frame i of setting s.
+struct SweepSpec {
+    int n_set = 0;
+    int thresh[kMaxSweep] = {};
+    int arc[kMaxSweep] = {};
+    int4* const* outs = nullptr;
+    int32_t* counts[kMaxSweep] = {};
+};
+
+constexpr int kSweepTH = 62;  // the sweep kernel's tile height (variant 0's geometry)
+
+// Pyramid (when asked), fused sweep and sweep decode, launched directly.
+vio_status enqueue_sweep(vio_ctx* ctx, int levels, cudaStream_t s, bool pyramid, const SweepInfo* d_sw) {
+    const bool prof = ctx->cfg.profile != 0;
+    if (prof) VIO_CK(cudaEventRecord(ctx->stage_ev[0], s));
+    if (levels > 1 && pyramid) {
+        pyr_fn(levels)<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->d_call);
+        VIO_CK(cudaGetLastError());
+    }
+    if (prof) VIO_CK(cudaEventRecord(ctx->stage_ev[1], s));
+    const int smem = SweepGeom<kSweepTH>::SMEM;
+    if (!ctx->grid_sweep) {
+        int occ = 0;
+        VIO_CK(cudaFuncSetAttribute(fast_sweep_kernel<kSweepTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_sweep_kernel<kSweepTH>, kThreads, smem));
+        ctx->grid_sweep = std::max(1, occ) * ctx->sm_count;
+    }
+    fast_sweep_kernel<kSweepTH><<<ctx->grid_sweep, kThreads, smem, s>>>(ctx->d_call, d_sw, ctx->d_counter,
+                                                                      ctx->d_status);
+    VIO_CK(cudaGetLastError());
+    if (prof) VIO_CK(cudaEventRecord(ctx->stage_ev[2], s));
+    sweep_decode_kernel<<<ctx->sm_count * 4, 256, 0, s>>>(ctx->d_call, d_sw, ctx->d_counter);
+    VIO_CK(cudaGetLastError());
+    if (prof) VIO_CK(cudaEventRecord(ctx->stage_ev[3], s));
+    return VIO_OK;
+}
+
 vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims,
                   int n, int thresh, int arc, int cell, int levels, int4* const* outs, int32_t* counts,
-                  cudaStream_t s, bool pyramid = true, Upload up = {}) {
+                  cudaStream_t s, bool pyramid = true, Upload up = {}, const SweepSpec* sweep = nullptr) {
     const Variant& v = variants()[variant];
     // arena layout
     size_t koff = 0, poff = 0;
@@ -233,7 +275,8 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
     vio_status st;
     const void* keys0 = ctx->d_keys;
     const void* pyr0 = ctx->d_pyr;
-    if ((st = grow(ctx, (void**)&ctx->d_keys, &ctx->keys_cap, koff * 8, true)) != VIO_OK) return st;
+    const int n_set = sweep ? sweep->n_set : 1;
+    if ((st = grow(ctx, (void**)&ctx->d_keys, &ctx->keys_cap, koff * 8 * n_set, true)) != VIO_OK) return st;
     if ((st = grow(ctx, (void**)&ctx->d_pyr, &ctx->pyr_cap, std::max<size_t>(poff, 256), false)) != VIO_OK) return st;
     if (keys0 != ctx->d_keys || pyr0 != ctx->d_pyr) ctx->map_cache.clear();
 
@@ -258,6 +301,9 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
     off += align_up(sizeof(int32_t) * (n + 1), 128);
     const size_t off_cells = off;
     off += align_up(sizeof(int32_t) * (n + 1), 128);
+    const size_t off_sweep = off;
+    const size_t off_souts = off + align_up(sizeof(SweepInfo), 128);
+    if (sweep) off = off_souts + align_up(sizeof(int4*) * n_set * n, 128);
     const size_t bytes = off;
 
     CallHeader* hdr = reinterpret_cast<CallHeader*>(st_base);
@@ -332,10 +378,28 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
     hdr->n_items = acc;
     hdr->n_pyr_blocks = blocks[n];
     hdr->n_cells = cells[n];
+    if (sweep) {
+        SweepInfo* si = reinterpret_cast<SweepInfo*>(st_base + off_sweep);
+        int4** so = reinterpret_cast<int4**>(st_base + off_souts);
+        std::memset(si, 0, sizeof(SweepInfo));
+        si->n_set = n_set;
+        for (int j = 0; j < n_set; ++j) {
+            si->thresh[j] = sweep->thresh[j];
+            si->arc[j] = sweep->arc[j];
+            si->counts[j] = sweep->counts[j];
+        }
+        si->set_stride = (int64_t)koff;
+        si->outs = reinterpret_cast<int4* const*>(ctx->d_call + off_souts);
+        for (int j = 0; j < n_set * n; ++j) so[j] = sweep->outs[j];
+    }
 
     VIO_CK(cudaMemcpyAsync(ctx->d_call, st_base, bytes, cudaMemcpyHostToDevice, s));
     VIO_CK(cudaEventRecord(ctx->ring_ev[slot], s));
-    if (ctx->cfg.use_graphs) {
+    if (sweep) {
+        if ((st = enqueue_sweep(ctx, levels, s, pyramid,
+                                reinterpret_cast<const SweepInfo*>(ctx->d_call + off_sweep))) != VIO_OK)
+            return st;
+    } else if (ctx->cfg.use_graphs) {
         cudaGraphExec_t g = nullptr;
         if ((st = get_graph(ctx, variant, levels, pyramid, &g)) != VIO_OK) return st;
         VIO_CK(cudaGraphLaunch(g, s));
@@ -633,6 +697,31 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
         vi = ctx->tuned[key];
     }
     ctx->last_variant = vi;
+    if (ctx->cfg.score == VIO_SCORE_SAD_B && ctx->cfg.nms_radius == 1 && n_params > 1) {
+        // fused sweep: settings sorted by threshold, up to kMaxSweep per launch,
+        // the pyramid built by the first launch
+        std::vector<int> order(n_params);
+        for (int p = 0; p < n_params; ++p) order[p] = p;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return thresholds[a] < thresholds[b]; });
+        std::vector<int4*> outs((size_t)kMaxSweep * n);
+        const int v0 = first_variant(1);
+        for (int g0 = 0; g0 < n_params; g0 += kMaxSweep) {
+            SweepSpec sp;
+            sp.n_set = std::min(kMaxSweep, n_params - g0);
+            for (int j = 0; j < sp.n_set; ++j) {
+                const int p = order[g0 + j];
+                sp.thresh[j] = thresholds[p];
+                sp.arc[j] = arc_lens[p];
+                sp.counts[j] = out_counts ? out_counts + (size_t)p * n : nullptr;
+                for (int i = 0; i < n; ++i) outs[(size_t)j * n + i] = reinterpret_cast<int4*>(out_cells[(size_t)p * n + i]);
+            }
+            sp.outs = outs.data();
+            if ((st = launch(ctx, v0, lev0.data(), pitch0.data(), dims, n, sp.thresh[0], sp.arc[0], cell, levels,
+                             outs.data(), nullptr, s, g0 == 0, {}, &sp)) != VIO_OK)
+                return st;
+        }
+        return VIO_OK;
+    }
     // the pyramid is built by the first detection and read by all of them
     std::vector<int4*> outs(n);
     for (int p = 0; p < n_params; ++p) {

@@ -110,6 +110,7 @@ struct vio_ctx {
     // one graph per (variant, levels): every batch shape replays it
     cudaGraphExec_t graphs[8][vio::kMaxLevels + 1] = {};
     int grid_fused[8] = {};
+    int grid_sweep = 0;
     std::unordered_map<ShapeKey, int, ShapeHash> tuned;  // batch shape -> variant
     std::unordered_map<MapKey, CUtensorMap, MapHash> map_cache;
     int pinned_variant = -1;

@@ -1,0 +1,324 @@
+// Fused threshold / arc-length sweep: up to 8 detector settings (threshold,
+// arc length) over the same frames in one pass.  Each tile is loaded once,
+// the coarse test runs once at the lowest threshold (its candidates are a
+// superset of every setting's), the 16 circle values of a candidate are read
+// once, Eq. 1's labels are formed once per distinct threshold, and the arc
+// test, NMS and cell maximum run per setting on a per-pixel bit mask of the
+// settings in which the pixel is a corner.  SAD-B is the score: it does not
+// depend on the setting, so one 16-bit score tile serves all of them.
+#pragma once
+#include <stdint.h>
+
+#include "vio_kernels.cuh"
+
+namespace vio {
+
+constexpr int kMaxSweep = 8;
+
+// Sweep section of a call block (the detector sections come first).
+struct SweepInfo {
+    int32_t n_set;                 // settings in this launch, 1..kMaxSweep
+    int32_t thresh[kMaxSweep];     // non-decreasing
+    int32_t arc[kMaxSweep];
+    int32_t pad;
+    int64_t set_stride;            // keys of setting s: FrameDesc::keys + s * set_stride
+    int4* const* outs;             // [n_set * n_frames] output records, setting-major
+    int32_t* counts[kMaxSweep];    // per setting: [n_frames] non-empty cells, or nullptr
+};
+
+template <int TH>
+struct SweepGeom : TileGeom<TH, 1> {
+    using B = TileGeom<TH, 1>;
+    static constexpr int MK_OFF = B::Q_OFF + B::WARPS * B::QCAP * 2;  // uint8 setting mask per score pixel
+    static constexpr int SMEM = MK_OFF + B::SR * B::SW + 128;
+};
+
+// Eq. 1 labels of the 16 circle points at threshold t: bright mask in bits
+// 0..15, dark mask in bits 16..31 (the biased 16-bit lane IMAD of eval_corner).
+__device__ __forceinline__ uint32_t sweep_labels(const uint32_t (&v)[16], uint32_t c, uint32_t t) {
+    const uint32_t K = ((0x7FFFu - c - t) & 0xFFFFu) | ((0x7FFFu + c - t) << 16);
+    uint32_t a[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const uint32_t w = K + v[i] * 0xFFFF0001u;
+        a[i & 3] = (a[i & 3] >> 4) | (w & 0x80008000u);
+    }
+    return (a[0] >> 3) | (a[1] >> 2) | (a[2] >> 1) | a[3];
+}
+
+template <int TH>
+__global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* __restrict__ call,
+                                                                const SweepInfo* __restrict__ sw,
+                                                                int32_t* __restrict__ counter,
+                                                                uint32_t* __restrict__ status) {
+    using G = SweepGeom<TH>;
+    constexpr int NB = G::NBUF;
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[NB], empty_bar[NB];
+    __shared__ ItemInfo info[NB];
+    constexpr int kTileCache = 512;
+    __shared__ int32_t tiles_sh[kTileCache];
+    __shared__ int32_t set_t[kMaxSweep], set_n[kMaxSweep];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint16_t* sc = reinterpret_cast<uint16_t*>(smem + G::SC_OFF);
+    uint8_t* mk = smem + G::MK_OFF;
+
+    const CallView cv(call);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_items = cv.h->n_items;
+    const int n_set = sw->n_set;
+
+    if (tid == 0) {
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&full_bar[b], 1);
+            mbar_init(&empty_bar[b], kConsumers / 32);
+        }
+        fence_barrier_init();
+    }
+    if (tid < kMaxSweep) {
+        set_t[tid] = tid < n_set ? sw->thresh[tid] : 0;
+        set_n[tid] = tid < n_set ? sw->arc[tid] : 16;
+    }
+    // score and setting-mask tiles start zero; only corners are written, and reset after use
+    for (int i = tid; i < G::SR * G::SW / 8; i += kThreads) reinterpret_cast<uint4*>(sc)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < G::SR * G::SW / 16; i += kThreads) reinterpret_cast<uint4*>(mk)[i] = make_uint4(0, 0, 0, 0);
+    if (blockIdx.x == 0)
+        for (int f = tid; f < n_set * cv.h->n_frames; f += kThreads) {
+            int32_t* cs = sw->counts[f / cv.h->n_frames];
+            if (cs) cs[f % cv.h->n_frames] = 0;
+        }
+    const int n_tiles = cv.h->n_frames * cv.h->levels + 1;
+    const bool cached = n_tiles <= kTileCache;
+    if (cached)
+        for (int i = tid; i < n_tiles; i += kThreads) tiles_sh[i] = cv.tiles[i];
+    __syncthreads();
+
+    if (warp == kConsumers / 32) {
+        // ---- producer warp: claims items, fills the ring, runs ahead ----
+        if (lane == 0) {
+            const int32_t* tiles = cached ? tiles_sh : cv.tiles;
+            int claimed = atomicAdd(counter, 1);
+            for (int t = 0;; ++t) {
+                const int b = t % NB;
+                const int it = claimed;
+                if (it < n_items) claimed = atomicAdd(counter, 1);
+                if (t >= NB && !mbar_wait_bounded(&empty_bar[b], ((t / NB) - 1) & 1, kWaitLimitNs)) {
+                    atomicOr(status, kStatusTimeout);
+                    break;
+                }
+                ItemInfo& in = info[b];
+                in.id = it;
+                if (it >= n_items) {
+                    mbar_arrive(&full_bar[b]);
+                    break;
+                }
+                const Item wi = decode_item(cv, tiles, it);
+                const FrameDesc& fd = cv.fds[wi.frame];
+                in.level = wi.level;
+                in.x0 = wi.tx * G::TW;
+                in.y0 = wi.ty * TH;
+                in.wk = fd.w >> wi.level;
+                in.hk = fd.h >> wi.level;
+                in.gw = fd.gw;
+                in.keys = fd.keys;
+                const CUtensorMap* map =
+                    wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
+                fence_tensormap_acquire(map);
+                mbar_arrive_expect_tx(&full_bar[b], G::BOX);
+                tma_load_2d(smem + G::IMG_OFF + b * G::BOXA, map, &full_bar[b], (in.x0 - 8) & ~15, in.y0 - 4);
+            }
+        }
+        return;
+    }
+
+    // ---- consumer warps ----
+    uint16_t* queue = reinterpret_cast<uint16_t*>(smem + G::Q_OFF) + warp * G::QCAP;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    // the coarse test at the lowest threshold with the two-adjacent rule
+    // keeps every pixel any setting can accept
+    const int tmin = set_t[0];
+    const bool high_t = tmin >= 128;
+    const uint32_t k7 = (uint32_t)((high_t ? 255 : 127) - tmin) * 0x01010101u;
+    const int64_t stride = sw->set_stride;
+
+    for (int t = 0;; ++t) {
+        const int b = t % NB;
+        if (!mbar_wait_bounded(&full_bar[b], (t / NB) & 1, kWaitLimitNs)) {
+            if (lane == 0) atomicOr(status, kStatusTimeout);
+            return;
+        }
+        const ItemInfo in = info[b];
+        if (in.id >= n_items) break;
+        const uint8_t* img = smem + G::IMG_OFF + b * G::BOXA;
+        const int k = in.level, Wk = in.wk, Hk = in.hk, x0 = in.x0, y0 = in.y0;
+        const uint32_t magic = cv.h->cell_magic[k];
+        const int xoff = x0 - 4 - ((x0 - 8) & ~15);
+
+        int total;
+        {
+            const int row_lo = max(0, 4 - y0), row_hi = min(G::SR, Hk - 2 - y0);
+            const int sx = 8 * (lane & 15);
+            const int xlo = max(3, 7 - x0), xhi = min(125, Wk + 1 - x0);
+            uint32_t vm0 = 0, vm1 = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                vm0 |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
+                vm1 |= (sx + 4 + j >= xlo && sx + 4 + j < xhi) ? 0x80u << (8 * j) : 0u;
+            }
+            const int xw = xoff / 4;
+            total = high_t ? coarse_and_compact<true, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo, row_hi,
+                                                                     vm0, vm1)
+                           : coarse_and_compact<false, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo, row_hi,
+                                                                      vm0, vm1);
+        }
+        __syncwarp();
+
+        // full test of every setting; corners (in any setting) compacted in place
+        int ncorner = 0;
+        const uint8_t* img_base = img + 3 * G::BW + xoff;
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = e0 + lane;
+            uint32_t cmask = 0;
+            int idx = 0;
+            if (e < total) {
+                idx = queue[e];
+                const uint8_t* p = img_base + idx + 16 * (idx >> 7);
+                const uint32_t c = p[0];
+                uint32_t v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * G::BW + circ_dx(i)];
+                int prev_t = -1;
+                uint32_t acc = 0;
+                for (int s = 0; s < n_set; ++s) {  // uniform
+                    const int ts = set_t[s], ns = set_n[s];
+                    if (ts != prev_t) {
+                        acc = sweep_labels(v, c, (uint32_t)ts);
+                        prev_t = ts;
+                    }
+                    const uint32_t bm = acc & 0xFFFFu, dm = acc >> 16;
+                    if (arc_starts(__popc(bm) >= ns ? bm : dm, ns)) cmask |= 1u << s;
+                }
+            }
+            const uint32_t cm = __ballot_sync(0xFFFFFFFFu, cmask != 0);
+            if (cmask) {
+                queue[ncorner + __popc(cm & lt_mask)] = (uint16_t)idx;
+                mk[idx] = (uint8_t)cmask;
+            }
+            ncorner += __popc(cm);
+        }
+        for (int e = lane; e < ncorner; e += 32) {
+            const int idx = queue[e];
+            sc[idx] = (uint16_t)sad_b<G::BW>(img_base + idx + 16 * (idx >> 7));
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_bar[b]);
+        named_barrier(1, kConsumers);  // all scores and masks of the tile are written
+
+        // 3x3 NMS of every setting at once: a neighbour suppresses the pixel
+        // in the settings where it is a corner with a higher score
+        for (int e0 = 0; e0 < ncorner; e0 += 32) {
+            const int e = e0 + lane;
+            uint32_t keep = 0, cell_id = 0xFFFFFFFFu, hi = 0, lo = 0;
+            if (e < ncorner) {
+                const int idx = queue[e];
+                const int sr = idx >> 7, scx = idx & 127;
+                if (scx >= 4 && scx < 4 + G::TW && sr >= 1 && sr < 1 + TH) {
+                    const uint16_t* q = sc + idx;
+                    const uint8_t* qm = mk + idx;
+                    const uint32_t s = q[0];
+                    uint32_t allowed = 0xFFu;
+#pragma unroll
+                    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx)
+                            if (dy != 0 || dx != 0) {
+                                const int o = dy * G::SW + dx;
+                                allowed &= s >= q[o] ? 0xFFu : ~(uint32_t)qm[o];
+                            }
+                    keep = qm[0] & allowed;
+                    if (keep) {
+                        const uint32_t x = (uint32_t)(x0 - 4 + scx), y = (uint32_t)(y0 - 1 + sr);
+                        cell_id = __umulhi(y, magic) * (uint32_t)in.gw + __umulhi(x, magic);
+                        hi = s;
+                        lo = 0xFFFFFFFFu - (((uint32_t)k << 28) | (y * (uint32_t)Wk + x));
+                    }
+                }
+            }
+            const uint32_t any = __ballot_sync(0xFFFFFFFFu, keep != 0);
+            if (any) {
+                const int leader = __ffs(any) - 1;
+                const uint32_t c = __shfl_sync(0xFFFFFFFFu, cell_id, leader);
+                const bool one_cell = __all_sync(0xFFFFFFFFu, keep == 0 || cell_id == c);
+                for (int s = 0; s < n_set; ++s) {  // uniform
+                    const uint32_t hs = (keep >> s) & 1u ? hi : 0u;
+                    const uint32_t surv = __ballot_sync(0xFFFFFFFFu, hs != 0);
+                    if (!surv) continue;
+                    unsigned long long* keys = reinterpret_cast<unsigned long long*>(in.keys + s * stride);
+                    if (one_cell) {
+                        const uint32_t hmax = __reduce_max_sync(0xFFFFFFFFu, hs);
+                        const uint32_t lmax = __reduce_max_sync(0xFFFFFFFFu, hs == hmax ? lo : 0u);
+                        if (lane == __ffs(surv) - 1) atomicMax(&keys[c], ((unsigned long long)hmax << 32) | lmax);
+                    } else if (hs != 0) {
+                        atomicMax(&keys[cell_id], ((unsigned long long)hs << 32) | lo);
+                    }
+                }
+            }
+        }
+        named_barrier(1, kConsumers);  // every warp's NMS has read its neighbours
+        for (int e = lane; e < ncorner; e += 32) {
+            const int idx = queue[e];
+            sc[idx] = 0;
+            mk[idx] = 0;
+        }
+    }
+}
+
+// Decode of a sweep: one thread per (setting, cell) of all frames.
+static __global__ void __launch_bounds__(256) sweep_decode_kernel(const uint8_t* __restrict__ call,
+                                                                 const SweepInfo* __restrict__ sw,
+                                                                 int32_t* __restrict__ counter) {
+    const CallView cv(call);
+    const int nf = cv.h->n_frames, cells = cv.h->n_cells;
+    const int total = sw->n_set * cells;
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        int g = -1;  // (setting, frame) group of this thread
+        bool hit = false;
+        if (i < total) {
+            const int s = i / cells, ci = i - s * cells;
+            const int f = upper_index(cv.cells, nf, ci);
+            const FrameDesc& fd = cv.fds[f];
+            const int c = ci - cv.cells[f];
+            uint64_t* kp = fd.keys + s * sw->set_stride + c;
+            const uint64_t key = *kp;
+            int4 rec = make_int4(-1, -1, -1, 0);
+            if (key != 0) {
+                const uint32_t lin = 0xFFFFFFFFu - (uint32_t)key;
+                const int k = (int)(lin >> 28);
+                const uint32_t idx = lin & 0x0FFFFFFFu;
+                const uint32_t wk = (uint32_t)(fd.w >> k);
+                const int y = (int)(idx / wk), x = (int)(idx - (uint32_t)y * wk);
+                rec = make_int4(x << k, y << k, k, (int)(key >> 32));
+                *kp = 0;
+                hit = true;
+            }
+            sw->outs[s * nf + f][c] = rec;
+            g = s * nf + f;
+        }
+        // lanes of one (setting, frame) add their hits with one atomic
+        uint32_t pend = __ballot_sync(0xFFFFFFFFu, g >= 0);
+        while (pend) {
+            const int leader = __ffs(pend) - 1;
+            const int gl = __shfl_sync(0xFFFFFFFFu, g, leader);
+            const uint32_t grp = __ballot_sync(0xFFFFFFFFu, g == gl);
+            const uint32_t hits = __popc(__ballot_sync(0xFFFFFFFFu, g == gl && hit));
+            int32_t* cs = sw->counts[gl / nf];
+            if (lane == leader && hits && cs) atomicAdd(&cs[gl % nf], (int)hits);
+            pend &= ~grp;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+}
+
+}  // namespace vio

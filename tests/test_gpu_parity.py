@@ -98,6 +98,32 @@ def test_large_frames_sweep_pyramid_once(dets):
         assert_parity(got, cnt[p], check, thresh, arc, 64, 4, 0)
 
 
+# settings out of threshold order, repeated thresholds, one at or above 128,
+# every arc length, more than the 8 settings one fused launch takes
+SWEEP_WIDE = [(40, 9), (5, 12), (20, 16), (5, 9), (130, 9), (12, 10), (12, 11), (20, 13), (7, 14), (60, 15)]
+
+
+def test_fused_sweep_groups_orders_and_fallbacks(dets, mixed):
+    imgs = mixed[::7]
+    frames = [to_gpu(im) for im in imgs]
+    outs, counts = dets[0].detect_sweep(frames, SWEEP_WIDE, 32, 3)
+    dets[0].sync()
+    cnt = counts.cpu().numpy()
+    for p, (thresh, arc) in enumerate(SWEEP_WIDE):
+        got = [o.cpu().numpy() for o in outs[p]]
+        assert_parity(got, cnt[p], imgs, thresh, arc, 32, 3, 0)
+    # contexts the fused launch does not serve (MT score, 5x5 NMS) run one
+    # detection per setting and must agree with the oracle all the same
+    wide = vio.Detector(max_frames=16, nms_radius=2)
+    for det, mode, radius in ((dets[2], 2, 1), (wide, 0, 2)):
+        o2, c2 = det.detect_sweep(frames[:3], SWEEP_WIDE[:3], 32, 3)
+        det.sync()
+        for p, (thresh, arc) in enumerate(SWEEP_WIDE[:3]):
+            assert_parity([o.cpu().numpy() for o in o2[p]], c2.cpu().numpy()[p], imgs[:3], thresh, arc, 32, 3,
+                          mode, nms_radius=radius)
+    wide.close()
+
+
 def test_large_frames_sampled(dets):
     """3840x2160, 4 levels, 64x64 cells: two frames of the 32-frame set in
     one launch, all eight (arc, thresh) combinations checked on frame 0 and
