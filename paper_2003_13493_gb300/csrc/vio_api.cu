@@ -468,6 +468,53 @@ vio_status detect_impl(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitc
 
 }  // namespace
 
+namespace vio {
+
+vio_status detect_from_host(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims, int n, int thresh,
+                            int arc, int cell, int levels, int4* const* outs, int32_t* d_counts, cudaStream_t s) {
+    // Frames in pinned host memory are read by the pyramid kernel through
+    // their device mapping (it writes the device copy of level 0 as it goes),
+    // so the upload overlaps the pyramid.  Anything else takes the copy engines.
+    std::vector<size_t> off(n);
+    std::vector<int> pitch0(n);
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        pitch0[i] = (int)align_up(dims[i].w, 16);
+        off[i] = need;
+        need += align_up((size_t)pitch0[i] * dims[i].h, 256);
+    }
+    vio_status st;
+    if ((st = grow(ctx, (void**)&ctx->d_in, &ctx->in_cap, need, false)) != VIO_OK) return st;
+    std::vector<const uint8_t*> lev0(n), src0(n, nullptr);
+    std::vector<int> src_pitch(n, 0);
+    bool any_up = false;
+    for (int i = 0; i < n; ++i) {
+        lev0[i] = ctx->d_in + off[i];
+        const uint8_t* mapped = static_cast<const uint8_t*>(device_alias(host_frames[i]));
+        if (levels > 1 && mapped && ((uintptr_t)mapped & 15) == 0 && (dims[i].pitch & 15) == 0) {
+            src0[i] = mapped;
+            src_pitch[i] = dims[i].pitch;
+            any_up = true;
+        } else if (dims[i].pitch == pitch0[i]) {  // rows already 16-byte multiples: one contiguous copy
+            VIO_CK(cudaMemcpyAsync(ctx->d_in + off[i], host_frames[i], (size_t)pitch0[i] * dims[i].h,
+                                   cudaMemcpyHostToDevice, s));
+        } else {
+            VIO_CK(cudaMemcpy2DAsync(ctx->d_in + off[i], pitch0[i], host_frames[i], dims[i].pitch, dims[i].w,
+                                     dims[i].h, cudaMemcpyHostToDevice, s));
+        }
+    }
+    Upload up;
+    if (any_up) {
+        up.src = src0.data();
+        up.pitch = src_pitch.data();
+    }
+    return detect_impl(ctx, lev0.data(), pitch0.data(), dims, n, thresh, arc, cell, levels, outs, d_counts, s, up);
+}
+
+const void* host_device_alias(const void* host) { return device_alias(host); }
+
+}  // namespace vio
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -742,19 +789,13 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
     VIO_CK(cudaSetDevice(ctx->cfg.device));
     for (int i = 0; i < n; ++i)
         if (!host_frames[i] || !host_cells[i]) return fail(ctx, VIO_ERR_INVALID_ARG, "NULL frame or output pointer");
-    std::vector<size_t> off(n);
-    std::vector<int> pitch0(n);
-    size_t need = 0, ncell_total = 0;
+    size_t ncell_total = 0;
     std::vector<size_t> coff(n);
     for (int i = 0; i < n; ++i) {
-        pitch0[i] = (int)align_up(dims[i].w, 16);
-        off[i] = need;
-        need += align_up((size_t)pitch0[i] * dims[i].h, 256);
         coff[i] = ncell_total;
         ncell_total += vio_num_cells(dims[i].w, dims[i].h, cell);
     }
     const size_t cell_bytes = ncell_total * sizeof(int4) + align_up(sizeof(int32_t) * n, 16);
-    if ((st = grow(ctx, (void**)&ctx->d_in, &ctx->in_cap, need, false)) != VIO_OK) return st;
     if ((st = grow(ctx, (void**)&ctx->d_cells, &ctx->cells_cap, cell_bytes, false)) != VIO_OK) return st;
     if (ctx->h_out_cap < cell_bytes) {
         if (ctx->h_out) cudaFreeHost(ctx->h_out);
@@ -763,45 +804,21 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
         VIO_CK(cudaHostAlloc(&ctx->h_out, cell_bytes, cudaHostAllocDefault));
         ctx->h_out_cap = cell_bytes;
     }
-    // Frames in pinned host memory are read by the pyramid kernel through
-    // their device mapping (it writes the device copy of level 0 as it goes),
-    // so the upload overlaps the pyramid; records go straight into pinned
-    // output buffers.  Anything else takes the copy engines.
-    std::vector<const uint8_t*> lev0(n), src0(n, nullptr);
-    std::vector<int> src_pitch(n, 0);
+    // records go straight into pinned output buffers; others come back
+    // through the context's staging
     std::vector<int4*> outs(n);
     std::vector<bool> direct_out(n, false);
-    bool any_up = false;
+    bool all_direct = true;
     for (int i = 0; i < n; ++i) {
-        lev0[i] = ctx->d_in + off[i];
-        const uint8_t* mapped = static_cast<const uint8_t*>(device_alias(host_frames[i]));
-        if (levels > 1 && mapped && ((uintptr_t)mapped & 15) == 0 && (dims[i].pitch & 15) == 0) {
-            src0[i] = mapped;
-            src_pitch[i] = dims[i].pitch;
-            any_up = true;
-        } else if (dims[i].pitch == pitch0[i]) {  // rows already 16-byte multiples: one contiguous copy
-            VIO_CK(cudaMemcpyAsync(ctx->d_in + off[i], host_frames[i], (size_t)pitch0[i] * dims[i].h,
-                                   cudaMemcpyHostToDevice, s));
-        } else {
-            VIO_CK(cudaMemcpy2DAsync(ctx->d_in + off[i], pitch0[i], host_frames[i], dims[i].pitch, dims[i].w,
-                                     dims[i].h, cudaMemcpyHostToDevice, s));
-        }
         int4* out_mapped = static_cast<int4*>(const_cast<void*>(device_alias(host_cells[i])));
         direct_out[i] = out_mapped && ((uintptr_t)out_mapped & 15) == 0;
+        all_direct &= direct_out[i];
         outs[i] = direct_out[i] ? out_mapped : ctx->d_cells + coff[i];
     }
     int32_t* d_counts = reinterpret_cast<int32_t*>(ctx->d_cells + ncell_total);
-    Upload up;
-    if (any_up) {
-        up.src = src0.data();
-        up.pitch = src_pitch.data();
-    }
-    if ((st = detect_impl(ctx, lev0.data(), pitch0.data(), dims, n, thresh, arc, cell, levels, outs.data(),
-                          d_counts, s, up)) != VIO_OK)
+    if ((st = vio::detect_from_host(ctx, host_frames, dims, n, thresh, arc, cell, levels, outs.data(), d_counts, s)) !=
+        VIO_OK)
         return st;
-    // records that did not go straight to the caller, then the counts
-    bool all_direct = true;
-    for (int i = 0; i < n; ++i) all_direct &= direct_out[i];
     if (all_direct)
         VIO_CK(cudaMemcpyAsync(ctx->h_out + ncell_total * sizeof(int4), d_counts, sizeof(int32_t) * n,
                                cudaMemcpyDeviceToHost, s));

@@ -174,3 +174,15 @@ namespace vio {
 // Frees the tracker's resident buffers (vio_destroy).
 void track_release(vio_ctx* ctx);
 }  // namespace vio
+
+namespace vio {
+// Detects frames that live in host memory, asynchronously on s: pinned frames
+// are uploaded by the pyramid kernel through their device mapping, others by
+// the copy engines into the context's staging.  outs[i] may be device memory
+// or the device mapping of pinned host memory; d_counts is device memory or
+// nullptr.  Arguments are checked by the caller.
+vio_status detect_from_host(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims, int n, int thresh,
+                            int arc, int cell, int levels, int4* const* outs, int32_t* d_counts, cudaStream_t s);
+// Device address of pinned host memory, else nullptr.
+const void* host_device_alias(const void* host);
+}  // namespace vio

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/vio.h"
+#include "vio_ctx.h"
 
 namespace {
 
@@ -50,8 +51,6 @@ struct Lane {
     vio_ctx* ctx = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    uint8_t* d_in = nullptr;
-    size_t in_cap = 0;
     vio_feature* d_cells = nullptr;   // cells of all frames, then int32 counts
     size_t cells_cap = 0;
     uint8_t* h_cells = nullptr;       // pinned copy of d_cells
@@ -125,45 +124,46 @@ vio_status grow_host(uint8_t** p, size_t* cap, size_t need) {
     return VIO_OK;
 }
 
-// Copies the batch in, detects, copies the cells out; all on the lane's stream.
+// Detects the batch on the lane's stream: pinned frames are read by the
+// pyramid kernel through their device mapping, records are written straight
+// into the lane's pinned result buffer, then the counts follow.
 vio_status launch_lane(vio_server_state* S, Lane& L) {
     const auto& c = S->cfg;
     const int n = (int)L.batch.size();
-    size_t in_need = 0, cell_need = 0;
-    std::vector<size_t> in_off(n);
+    size_t cell_need = 0;
     L.cell_off.assign(n, 0);
     for (int i = 0; i < n; ++i) {
-        const vio_dims& d = L.batch[i].dims;
-        in_off[i] = in_need;
-        in_need += align_up((size_t)align_up(d.w, 16) * d.h, 256);
         L.cell_off[i] = cell_need;
         cell_need += L.batch[i].ncell;
     }
     const size_t cell_bytes = cell_need * sizeof(vio_feature) + sizeof(int32_t) * n;
     vio_status st;
-    if (in_need > L.in_cap || cell_bytes > L.cells_cap) cudaStreamSynchronize(L.stream);
-    if ((st = grow_dev((void**)&L.d_in, &L.in_cap, in_need)) != VIO_OK) return st;
+    if (cell_bytes > L.cells_cap || cell_bytes > L.h_cap) cudaStreamSynchronize(L.stream);
     if ((st = grow_dev((void**)&L.d_cells, &L.cells_cap, cell_bytes)) != VIO_OK) return st;
     if ((st = grow_host(&L.h_cells, &L.h_cap, cell_bytes)) != VIO_OK) return st;
     std::vector<const uint8_t*> frames(n);
     std::vector<vio_dims> dims(n);
-    std::vector<vio_feature*> outs(n);
+    std::vector<int4*> outs(n);
+    bool all_direct = true;
     for (int i = 0; i < n; ++i) {
-        const vio_dims& d = L.batch[i].dims;
-        const int pitch = (int)align_up(d.w, 16);
-        if (cudaMemcpy2DAsync(L.d_in + in_off[i], pitch, L.batch[i].host, d.pitch, d.w, d.h, cudaMemcpyHostToDevice,
-                              L.stream) != cudaSuccess)
-            return VIO_ERR_CUDA;
-        frames[i] = L.d_in + in_off[i];
-        dims[i] = vio_dims{d.w, d.h, pitch};
-        outs[i] = L.d_cells + L.cell_off[i];
+        frames[i] = L.batch[i].host;
+        dims[i] = L.batch[i].dims;
+        int4* mapped = static_cast<int4*>(
+            const_cast<void*>(vio::host_device_alias(L.h_cells + L.cell_off[i] * sizeof(vio_feature))));
+        const bool direct = mapped && ((uintptr_t)mapped & 15) == 0;
+        all_direct &= direct;
+        outs[i] = direct ? mapped : reinterpret_cast<int4*>(L.d_cells + L.cell_off[i]);
     }
     int32_t* d_counts = reinterpret_cast<int32_t*>(L.d_cells + cell_need);
-    st = vio_detect(L.ctx, frames.data(), dims.data(), n, c.thresh, c.arc_len, c.cell_size, c.levels, outs.data(),
-                    d_counts, reinterpret_cast<vio_stream>(L.stream));
+    st = vio::detect_from_host(L.ctx, frames.data(), dims.data(), n, c.thresh, c.arc_len, c.cell_size, c.levels,
+                               outs.data(), d_counts, L.stream);
     if (st != VIO_OK) return st;
-    if (cudaMemcpyAsync(L.h_cells, L.d_cells, cell_bytes, cudaMemcpyDeviceToHost, L.stream) != cudaSuccess)
-        return VIO_ERR_CUDA;
+    const size_t cbytes = cell_need * sizeof(vio_feature);
+    const cudaError_t ce =
+        all_direct ? cudaMemcpyAsync(L.h_cells + cbytes, d_counts, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                                     L.stream)
+                   : cudaMemcpyAsync(L.h_cells, L.d_cells, cell_bytes, cudaMemcpyDeviceToHost, L.stream);
+    if (ce != cudaSuccess) return VIO_ERR_CUDA;
     if (cudaEventRecord(L.done, L.stream) != cudaSuccess) return VIO_ERR_CUDA;
     return VIO_OK;
 }
@@ -201,6 +201,7 @@ void finish_lane(vio_server_state* S, Lane& L) {
 void worker_main(vio_server_state* S) {
     cudaSetDevice(S->device);
     const auto& c = S->cfg;
+    uint64_t last_progress = now_ns();
     while (true) {
         bool progressed = false;
         // retire finished lanes
@@ -249,9 +250,19 @@ void worker_main(vio_server_state* S) {
             std::lock_guard<std::mutex> g(S->mu);
             if (!any_busy && (S->pending.empty() || S->error != VIO_OK)) break;
         }
-        if (!progressed) {
-            std::unique_lock<std::mutex> lk(S->mu);
-            S->cv.wait_for(lk, std::chrono::microseconds(20));
+        if (progressed) {
+            last_progress = now_ns();
+        } else {
+            // poll while batches are in flight or frames arrived recently;
+            // block (submit notifies) after a quiet millisecond
+            bool any_busy = false;
+            for (auto& L : S->lanes) any_busy |= L.busy;
+            if (any_busy || now_ns() - last_progress < 1000000ull) {
+                std::this_thread::yield();
+            } else {
+                std::unique_lock<std::mutex> lk(S->mu);
+                if (S->pending.empty() && !S->stop.load()) S->cv.wait_for(lk, std::chrono::milliseconds(1));
+            }
         }
     }
 }
@@ -262,7 +273,6 @@ void destroy_state(vio_server_state* S) {
         if (L.ctx) vio_destroy(L.ctx);
         if (L.stream) cudaStreamDestroy(L.stream);
         if (L.done) cudaEventDestroy(L.done);
-        cudaFree(L.d_in);
         cudaFree(L.d_cells);
         if (L.h_cells) cudaFreeHost(L.h_cells);
     }
