@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--spin", type=float, default=0.5, help="seconds of untimed steps before timing")
     ap.add_argument("--variant", type=int, default=-1, help="pin a tile variant instead of autotuning")
     ap.add_argument("--no-tracker", action="store_true", help="skip the feature-tracker leg")
+    ap.add_argument("--tracker-only", action="store_true",
+                    help="run only the feature-tracker leg and print its JSON object")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson serving run (0 skips it)")
     return ap.parse_args()
@@ -204,12 +206,17 @@ def oracle_rate(frames, wl, seconds: float):
         by_size.setdefault(f.shape, []).append(f)
     sample = [v[i] for v in by_size.values() for i in range(min(2, len(v)))]
     cores = os.cpu_count() or 1
+    settings = wl.get("sweep") or [(wl["thresh"], wl["arc"])]
+
+    def one(im):  # a frame is done when every setting of the workload is
+        for t, a in settings:
+            oracle.detect(im, t, a, wl["cell"], wl["levels"])
+
     done = 0
     t0 = time.perf_counter()
     with ThreadPoolExecutor(cores) as ex:
         while True:
-            list(ex.map(lambda im: oracle.detect(im, wl["thresh"], wl["arc"], wl["cell"], wl["levels"]),
-                        sample))
+            list(ex.map(one, sample))
             done += len(sample)
             if time.perf_counter() - t0 >= seconds:
                 break
@@ -343,7 +350,9 @@ def run_ours(args, rank, world, local_rank):
                             "picked_by": "autotuner" if args.variant < 0 else "--variant"},
                    "parallelism": f"replicas x{world}, no collective"},
         "clocks": clk,
-        "gpu_launches": args.steps * ((1 if wl["levels"] > 1 else 0) + 2 * npar),
+        # per step: the pyramid, then a detect and a decode kernel per launch
+        # (a sweep detects up to 8 settings per launch)
+        "gpu_launches": args.steps * ((1 if wl["levels"] > 1 else 0) + 2 * ((npar + 7) // 8 if sweep else 1)),
     }
     if sweep:
         res["detections_per_s"] = round(world * n * npar * args.steps / (ms / 1e3), 1)
@@ -696,7 +705,10 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded value noise + shapes, integer generator)", "impl": "reference",
-            "config": {"workload": f"{args.workload}: {wl['desc']}"},
+            "config": {"workload": f"{args.workload}: {wl['desc']}", "frames_per_step": len(frames),
+                       "detections_per_frame": len(wl.get("sweep") or [0]),
+                       "mpixel_per_step": round(sum(f.size for f in frames) / 1e6, 3), "levels": wl["levels"],
+                       "thresh": wl["thresh"], "arc_len": wl["arc"], "cell": wl["cell"], "score": "SAD-B"},
             "cpu_baseline": {"value": round(total, 2), "unit": "frames/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(total, 2), "unit": "frames/s", "h2d_bytes_per_step": 0,
@@ -708,6 +720,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.tracker_only:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"tracker": tracker_leg(args, local_rank)}))
+        return
     if args.impl == "reference":
         res = run_reference(args, rank, world)
         if res is not None:

@@ -121,14 +121,19 @@ __device__ bool track_level(const TrackLevel& lv, float cx, float cy, float* tg,
     if (!__all_sync(0xFFFFFFFFu, ok)) return false;
     __syncwarp();
 
+    // Each lane owns a strip of NPX consecutive patch rows in one column:
+    // column i = lane % P, rows j = (lane / P) * NPX + m.  The samples of a
+    // strip share their column, so each iteration reads NPX + 1 pairs of
+    // pixels and blends each pair once (the bilinear weights are the same for
+    // every sample of the patch: all sit at integer offsets from one point).
+    const int col = lane % P, row0 = (lane / P) * NPX;
     // U (Eq. 4) of this lane's pixels, with the appearance at the start of the level
     const float g = 1.f + alpha;
     float T[NPX], Ux[NPX], Uy[NPX];
     float h00 = 0, h01 = 0, h02 = 0, h03 = 0, h11 = 0, h12 = 0, h13 = 0, h22 = 0, h23 = 0, h33 = 0;
 #pragma unroll
     for (int m = 0; m < NPX; ++m) {
-        const int idx = lane + 32 * m, j = idx / P, i = idx - j * P;
-        const float* c = tg + (j + 1) * G + (i + 1);
+        const float* c = tg + (row0 + m + 1) * G + (col + 1);
         T[m] = c[0];
         Ux[m] = g * (0.5f * (c[1] - c[-1]));
         Uy[m] = g * (0.5f * (c[G] - c[-G]));
@@ -160,24 +165,27 @@ __device__ bool track_level(const TrackLevel& lv, float cx, float cy, float* tg,
     if (!cholesky4(L)) return false;
 
     for (int it = 0; it < max_iters; ++it) {
+        // this lane's samples: column xs, rows ys .. ys + NPX - 1 of the next image
+        const float xs = o0 + (float)col + tx, ys = o1 + (float)row0 + ty;
+        ok = inside(xs, ys, lv.w, lv.h) && inside(xs, ys + (float)(NPX - 1), lv.w, lv.h);
+        if (!__all_sync(0xFFFFFFFFu, ok)) return false;
+        const float fx = floorf(xs), fy = floorf(ys);
+        const float ax = xs - fx, ay = ys - fy;
+        const uint8_t* q = lv.next + (size_t)(int)fy * lv.pitch_next + (int)fx;
+        float top = fmaf(ax, (float)__ldg(q + 1) - (float)__ldg(q), (float)__ldg(q));
         float b0 = 0, b1 = 0, b2 = 0, b3 = 0, rr = 0;
-        ok = true;
 #pragma unroll
         for (int m = 0; m < NPX; ++m) {
-            const int idx = lane + 32 * m, j = idx / P, i = idx - j * P;
-            const float qx = o0 + (float)i + tx, qy = o1 + (float)j + ty;
-            float r = 0.f;
-            if (inside(qx, qy, lv.w, lv.h))
-                r = bilinear(lv.next, lv.pitch_next, qx, qy) - fmaf(1.f + alpha, T[m], beta);
-            else
-                ok = false;
+            q += lv.pitch_next;
+            const float bot = fmaf(ax, (float)__ldg(q + 1) - (float)__ldg(q), (float)__ldg(q));
+            const float r = fmaf(ay, bot - top, top) - fmaf(1.f + alpha, T[m], beta);
+            top = bot;
             b0 = fmaf(Ux[m], r, b0);
             b1 = fmaf(Uy[m], r, b1);
             b2 = fmaf(T[m], r, b2);
             b3 += r;
             rr = fmaf(r, r, rr);
         }
-        if (!__all_sync(0xFFFFFFFFu, ok)) return false;
         const float b[4] = {warp_sum(b0), warp_sum(b1), use_gain ? warp_sum(b2) : 0.f, use_off ? warp_sum(b3) : 0.f};
         residual = sqrtf(warp_sum(rr) * (1.f / (P * P)));
         float dq[4];
@@ -192,7 +200,7 @@ __device__ bool track_level(const TrackLevel& lv, float cx, float cy, float* tg,
     return true;
 }
 
-__global__ void __launch_bounds__(kTrackWarps * 32) track_kernel(const uint8_t* __restrict__ call,
+__global__ void __launch_bounds__(kTrackWarps * 32, 3) track_kernel(const uint8_t* __restrict__ call,
                                                                 uint32_t off_track) {
     __shared__ float grid_sh[kTrackWarps][kTrackMaxGrid];
     const CallView cv(call);
