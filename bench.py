@@ -485,29 +485,57 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     out["plain"] = {"value": round(psteps * n / (pms / 1e3), 1), "unit": "frames/s",
                     "what": "same frames, one vio_detect call (and graph replay) per frame"}
 
-    # end to end through the host-buffer entry point (pinned host frames)
+    # end to end through the host-buffer entry points (pinned host frames and
+    # outputs): each step copies its frames in and its records out
     pinned = [torch.from_numpy(f).pin_memory() for f in frames_np]
     host_frames = [p.numpy() for p in pinned]
-    host_outs = [torch.empty((vio.num_cells(w, h, wl["cell"]), 4), dtype=torch.int32).pin_memory().numpy()
-                 for w, h in dims]
-    host_counts = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+
+    def pinned_outs():
+        o = [torch.empty((vio.num_cells(w, h, wl["cell"]), 4), dtype=torch.int32).pin_memory().numpy()
+             for w, h in dims]
+        return o, torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+
     e2e_det = vio.Detector(device=dev.index, max_frames=max(64, n))
     e2e_det.set_variant(det.tuning()[2])
+    esteps = max(3, min(args.steps, 50))
+    h2d = sum(w * h for w, h in dims)
+    d2h = sum(16 * vio.num_cells(w, h, wl["cell"]) for w, h in dims) + 4 * n
+    # synchronous: one vio_detect_host call per step
+    host_outs, host_counts = pinned_outs()
     for _ in range(3):
         e2e_det.detect_host(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], host_outs,
                             host_counts, stream)
-    esteps = max(3, min(args.steps, 50))
     t0 = time.perf_counter()
     for _ in range(esteps):
         e2e_det.detect_host(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], host_outs,
                             host_counts, stream)
+    dt_sync = time.perf_counter() - t0
+    # pipelined: vio_detect_host_async on two alternating streams, so that a
+    # step's frame copies overlap the previous step's kernels
+    streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    bufs = [pinned_outs(), pinned_outs()]
+    for i in range(4):
+        o, c = bufs[i % 2]
+        e2e_det.detect_host_async(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], o, c,
+                                  stream=streams[i % 2])
+    for st in streams:
+        e2e_det.sync(st)
+    t0 = time.perf_counter()
+    for i in range(esteps):
+        o, c = bufs[i % 2]
+        e2e_det.detect_host_async(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], o, c,
+                                  stream=streams[i % 2])
+    for st in streams:
+        e2e_det.sync(st)
     dt = time.perf_counter() - t0
     e2e_det.close()
-    h2d = sum(w * h for w, h in dims)
-    d2h = sum(16 * vio.num_cells(w, h, wl["cell"]) for w, h in dims) + 4 * n
     out["e2e"] = {"value": round(esteps * n / dt, 1), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                   "d2h_bytes_per_step": d2h, "steps": esteps,
-                  "what": "vio_detect_host: pinned host frames -> device -> detect -> host cells, synchronous"}
+                  "what": "vio_detect_host_async on two alternating streams: pinned host frames copied in, "
+                          "records written into pinned host memory, counts copied back, all inside the timed "
+                          "region",
+                  "sync": {"value": round(esteps * n / dt_sync, 1), "unit": "frames/s",
+                           "what": "vio_detect_host, one synchronous call per step"}}
 
     if args.serve_seconds > 0:
         out["serving"] = serving_leg(args, dev.index)

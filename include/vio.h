@@ -172,15 +172,40 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
                             vio_feature* const* out_cells, int32_t* out_counts, vio_stream stream);
 
 /*
- * Same as vio_detect for frames and results in HOST memory: the frames are
- * copied into resident device slots, detected, and the cells copied back;
- * the call returns when out_cells (host, per frame) and out_counts (host
- * int32[n_frames] or NULL) are written.  Pinned host memory makes the
- * copies asynchronous; pageable memory works too.
+ * Same as vio_detect for frames and results in HOST memory; the call returns
+ * when host_cells (host, per frame) and host_counts (host int32[n_frames] or
+ * NULL) are written.  Frames in pinned (page-locked) memory whose address and
+ * pitch are multiples of 16 are read by the pyramid kernel through their
+ * device mapping, which also writes the device copy of level 0 (one pass over
+ * the host link, overlapped with the pyramid); other frames are copied by the
+ * copy engines.  Records for pinned, 16-byte aligned host_cells are written
+ * in place by the decode kernel; others come back through a staging copy.
  */
 vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims,
                            int n_frames, int thresh, int arc_len, int cell_size, int levels,
                            vio_feature* const* host_cells, int32_t* host_counts, vio_stream stream);
+
+/*
+ * Asynchronous form of vio_detect_host for pipelining batches: it enqueues
+ * the copy of the frames into one of three rotating device input slots (copy
+ * engines), the detection and the result writes on `stream` and returns.
+ * The results are valid after vio_sync(ctx, stream).  Calls on different
+ * streams overlap their frame copies with the previous call's kernels (the
+ * kernels of one context still run one call after another).
+ *
+ *   host_frames  HOST frames, pinned or pageable (pageable frames make the
+ *                copy synchronous); they must stay unchanged until the call
+ *                completes
+ *   host_cells   PINNED host arrays, 16-byte aligned, written in place by the
+ *                device; they must not be read or reused before completion
+ *   host_counts  PINNED host int32[n_frames] or NULL
+ *
+ * Errors: VIO_ERR_INVALID_ARG (as vio_detect, or host_cells / host_counts not
+ * pinned), VIO_ERR_OOM, VIO_ERR_CUDA.
+ */
+vio_status vio_detect_host_async(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims,
+                                 int n_frames, int thresh, int arc_len, int cell_size, int levels,
+                                 vio_feature* const* host_cells, int32_t* host_counts, vio_stream stream);
 
 /* Stage durations of the context's most recent vio_detect call, in ms:
  * ms[0] pyramid, ms[1] fused FAST + NMS + cell max, ms[2] decode.  Needs

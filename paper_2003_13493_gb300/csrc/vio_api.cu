@@ -635,6 +635,11 @@ vio_status vio_destroy(vio_ctx* ctx) {
     cudaDeviceSynchronize();
     ctx->drop_graphs();
     track_release(ctx);
+    for (auto& hs : ctx->hslots) {
+        cudaFree(hs.d_in);
+        cudaFree(hs.d_counts);
+        if (hs.done) cudaEventDestroy(hs.done);
+    }
     cudaFree(ctx->d_call);
     cudaFree(ctx->d_counter);
     cudaFree(ctx->d_keys);
@@ -835,6 +840,60 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
             std::memcpy(host_cells[i], rec + coff[i], vio_num_cells(dims[i].w, dims[i].h, cell) * sizeof(int4));
     if (host_counts)
         std::memcpy(host_counts, ctx->h_out + ncell_total * sizeof(int4), sizeof(int32_t) * n);
+    return VIO_OK;
+}
+
+vio_status vio_detect_host_async(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims, int n,
+                                 int thresh, int arc, int cell, int levels, vio_feature* const* host_cells,
+                                 int32_t* host_counts, vio_stream stream) {
+    vio_status st = check_args(ctx, host_frames, dims, n, thresh, arc, cell, levels, host_cells);
+    if (st != VIO_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    VIO_CK(cudaSetDevice(ctx->cfg.device));
+    std::vector<int4*> outs(n);
+    for (int i = 0; i < n; ++i) {
+        if (!host_frames[i] || !host_cells[i]) return fail(ctx, VIO_ERR_INVALID_ARG, "NULL frame or output pointer");
+        int4* mapped = static_cast<int4*>(const_cast<void*>(device_alias(host_cells[i])));
+        if (!mapped || ((uintptr_t)mapped & 15))
+            return fail(ctx, VIO_ERR_INVALID_ARG, "host_cells must be pinned, 16-byte aligned host memory");
+        outs[i] = mapped;
+    }
+    if (host_counts && !device_alias(host_counts))
+        return fail(ctx, VIO_ERR_INVALID_ARG, "host_counts must be pinned host memory");
+    HostSlot& slot = ctx->hslots[ctx->hslot_pos];
+    ctx->hslot_pos = (ctx->hslot_pos + 1) % kHostSlots;
+    if (!slot.done) VIO_CK(cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming));
+    // the kernels of the slot's previous call have read its frames
+    if (slot.used) VIO_CK(cudaStreamWaitEvent(s, slot.done, 0));
+    std::vector<size_t> off(n);
+    std::vector<int> pitch0(n);
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        pitch0[i] = (int)align_up(dims[i].w, 16);
+        off[i] = need;
+        need += align_up((size_t)pitch0[i] * dims[i].h, 256);
+    }
+    if ((st = grow(ctx, (void**)&slot.d_in, &slot.in_cap, need, false)) != VIO_OK) return st;
+    if ((st = grow(ctx, (void**)&slot.d_counts, &slot.counts_cap, sizeof(int32_t) * n, false)) != VIO_OK) return st;
+    std::vector<const uint8_t*> lev0(n);
+    for (int i = 0; i < n; ++i) {
+        lev0[i] = slot.d_in + off[i];
+        if (dims[i].pitch == pitch0[i])
+            VIO_CK(cudaMemcpyAsync(slot.d_in + off[i], host_frames[i], (size_t)pitch0[i] * dims[i].h,
+                                   cudaMemcpyHostToDevice, s));
+        else
+            VIO_CK(cudaMemcpy2DAsync(slot.d_in + off[i], pitch0[i], host_frames[i], dims[i].pitch, dims[i].w,
+                                     dims[i].h, cudaMemcpyHostToDevice, s));
+    }
+    // the detection waits for the context's previous call (another stream's
+    // included), so the copies above overlap that call's kernels
+    if ((st = detect_impl(ctx, lev0.data(), pitch0.data(), dims, n, thresh, arc, cell, levels, outs.data(),
+                          slot.d_counts, s)) != VIO_OK)
+        return st;
+    if (host_counts)
+        VIO_CK(cudaMemcpyAsync(host_counts, slot.d_counts, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    VIO_CK(cudaEventRecord(slot.done, s));
+    slot.used = true;
     return VIO_OK;
 }
 

@@ -47,6 +47,17 @@ struct MapHash {
 };
 
 
+// One input slot of vio_detect_host_async: frames of one call in flight.
+struct HostSlot {
+    uint8_t* d_in = nullptr;
+    size_t in_cap = 0;
+    int32_t* d_counts = nullptr;
+    size_t counts_cap = 0;
+    cudaEvent_t done = nullptr;  // after the kernels that read the slot
+    bool used = false;
+};
+constexpr int kHostSlots = 3;
+
 // Resident state of the feature tracker (vio_track).
 struct TrackState {
     uint8_t* d_call = nullptr;   // the current call block
@@ -116,6 +127,8 @@ struct vio_ctx {
     int pinned_variant = -1;
     int last_variant = 0;
     vio::TrackState track;
+    vio::HostSlot hslots[vio::kHostSlots];
+    int hslot_pos = 0;
 
     void drop_graphs() {
         for (auto& row : graphs)

@@ -113,6 +113,8 @@ def load(build_if_missing: bool = True):
     lib.vio_detect.restype = st
     lib.vio_detect_host.argtypes = detect_args
     lib.vio_detect_host.restype = st
+    lib.vio_detect_host_async.argtypes = detect_args
+    lib.vio_detect_host_async.restype = st
     lib.vio_detect_sweep.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(Dims), ci, ctypes.POINTER(ci),
                                      ctypes.POINTER(ci), ci, ci, ci, ctypes.POINTER(P), P, P]
     lib.vio_detect_sweep.restype = st
@@ -351,6 +353,26 @@ class Detector:
         self._check(self.lib.vio_detect_host(self.ctx, fptr, dims, n, thresh, arc_len, cell, levels, optr,
                                              ctypes.c_void_p(counts.ctypes.data),
                                              _stream_handle(stream) if stream is not None else ctypes.c_void_p(0)))
+        return outs, counts
+
+    def detect_host_async(self, frames, thresh: int, arc_len: int, cell: int, levels: int, outs, counts=None,
+                          stream=None):
+        """Asynchronous host-buffer detection: frames are 2-D uint8 numpy
+        arrays (pinned or pageable), outs (and counts) numpy views of pinned
+        memory that the device writes; valid after sync(stream)."""
+        n = len(frames)
+        dims = (Dims * n)()
+        fptr = (ctypes.c_void_p * n)()
+        for i, f in enumerate(frames):
+            if f.dtype != np.uint8 or f.ndim != 2 or f.strides[1] != 1:
+                raise ValueError("frames must be 2-D uint8 arrays with unit column stride")
+            dims[i] = Dims(f.shape[1], f.shape[0], f.strides[0])
+            fptr[i] = f.ctypes.data
+        optr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+        cptr = ctypes.c_void_p(counts.ctypes.data) if counts is not None else None
+        self._check(self.lib.vio_detect_host_async(self.ctx, fptr, dims, n, thresh, arc_len, cell, levels, optr, cptr,
+                                                   _stream_handle(stream) if stream is not None
+                                                   else ctypes.c_void_p(0)))
         return outs, counts
 
     def stage_ms(self) -> tuple[float, float, float]:

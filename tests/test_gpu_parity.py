@@ -276,6 +276,46 @@ def test_host_path_pinned_buffers(dets, mixed):
     assert_parity(got, counts, imgs, 15, 9, 32, 1, 0)
 
 
+def test_host_async_pipelined_on_two_streams(dets, mixed):
+    """Batches alternate between two streams with rotating input slots; every
+    batch's records must equal the oracle once its stream is synchronised."""
+    sets = [mixed[0:16:5], mixed[16:32:5], mixed[32:48:5], mixed[48:64:5]]
+    keep = []
+
+    def pinned_outs(imgs):
+        outs = []
+        for im in imgs:
+            b, v = pinned_like(np.zeros((vio.num_cells(im.shape[1], im.shape[0], 32), 4), np.int32))
+            keep.append(b)
+            outs.append(v)
+        b, c = pinned_like(np.zeros(len(imgs), np.int32))
+        keep.append(b)
+        return outs, c
+
+    frames = []
+    for imgs in sets:
+        fr = []
+        for im in imgs:
+            b, v = pinned_like(im)
+            keep.append(b)
+            fr.append(v)
+        frames.append(fr)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    results = []
+    for rep in range(2):
+        for k, imgs in enumerate(sets):
+            outs, counts = pinned_outs(imgs)
+            dets[0].detect_host_async(frames[k], 15, 9, 32, 3, outs, counts, stream=streams[k % 2])
+            results.append((imgs, outs, counts))
+    for st in streams:
+        dets[0].sync(st)
+    for imgs, outs, counts in results:
+        assert_parity(outs, counts, imgs, 15, 9, 32, 3, 0)
+    # pageable outputs cannot be written by the device
+    with pytest.raises(vio.VioError):
+        dets[0].detect_host_async(frames[0], 15, 9, 32, 3, [np.zeros_like(o) for o in results[0][1]])
+
+
 def test_invalid_arguments_rejected(dets):
     img = to_gpu(synth.make_frame(64, 64, seed=1))
     d = dets[0]
