@@ -218,6 +218,14 @@ vio_status vio_stage_ms(vio_ctx* ctx, float* ms3);
  * device-side status (VIO_ERR_TIMEOUT when a bounded wait gave up). */
 vio_status vio_sync(vio_ctx* ctx, vio_stream stream);
 
+/* Diagnostic of the failure path: runs one warp that waits, with the same
+ * bounded mbarrier wait the detect kernels use, on a barrier nothing ever
+ * completes, limited to limit_us microseconds (1..1000000).  The kernel
+ * records the timeout in the context's status word and returns; the call
+ * waits for it and returns VIO_ERR_TIMEOUT (the status word is cleared, the
+ * context stays usable).  Any other status means the mechanism failed. */
+vio_status vio_selftest_timeout(vio_ctx* ctx, uint32_t limit_us);
+
 /*
  * Tile configuration of the fused kernel.  tile_w x tile_h level pixels per
  * work item, cta_per_sm resident CTAs per SM for the persistent launch,

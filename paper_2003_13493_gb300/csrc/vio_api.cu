@@ -466,6 +466,18 @@ vio_status detect_impl(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitc
     return launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s, true, up);
 }
 
+// One warp waits on a barrier that nothing completes; the bounded wait gives
+// up after limit_ns and records the timeout (vio_selftest_timeout).
+__global__ void selftest_wait_kernel(uint32_t* status, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(status, kStatusTimeout);
+}
+
 }  // namespace
 
 namespace vio {
@@ -906,6 +918,23 @@ vio_status vio_sync(vio_ctx* ctx, vio_stream stream) {
         return fail(ctx, VIO_ERR_TIMEOUT, "a bounded device-side wait timed out");
     }
     return VIO_OK;
+}
+
+vio_status vio_selftest_timeout(vio_ctx* ctx, uint32_t limit_us) {
+    if (!ctx || limit_us < 1 || limit_us > 1000000) return VIO_ERR_INVALID_ARG;
+    VIO_CK(cudaSetDevice(ctx->cfg.device));
+    cudaStream_t s = nullptr;
+    VIO_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    selftest_wait_kernel<<<1, 32, 0, s>>>(ctx->d_status, (uint64_t)limit_us * 1000ull);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return fail(ctx, VIO_ERR_CUDA, std::string("selftest: ") + cudaGetErrorString(e));
+    if (*ctx->h_status) {
+        *ctx->h_status = 0;
+        return fail(ctx, VIO_ERR_TIMEOUT, "a bounded device-side wait timed out");
+    }
+    return fail(ctx, VIO_ERR_CUDA, "selftest: the bounded wait did not report its timeout");
 }
 
 vio_status vio_stage_ms(vio_ctx* ctx, float* ms3) {

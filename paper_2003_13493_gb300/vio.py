@@ -120,6 +120,8 @@ def load(build_if_missing: bool = True):
     lib.vio_detect_sweep.restype = st
     lib.vio_sync.argtypes = [P, P]
     lib.vio_sync.restype = st
+    lib.vio_selftest_timeout.argtypes = [P, ctypes.c_uint32]
+    lib.vio_selftest_timeout.restype = st
     lib.vio_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     lib.vio_stage_ms.restype = st
     lib.vio_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
