@@ -528,6 +528,50 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
     return __shfl_sync(0xFFFFFFFFu, incl, 31);
 }
 
+// Producer of the detect kernels (one thread): claims work items from the
+// counter one ahead of their use, decodes each into the tile it covers and
+// issues the TMA load of the tile and its halo into the next buffer of the
+// ring once the consumer warps have released it.  An item index >= n_items
+// tells the consumers to stop.
+template <int TH, int R>
+__device__ __forceinline__ void produce_tiles(const CallView& cv, const int32_t* tiles, int32_t* counter,
+                                              uint32_t* status, ItemInfo* info, uint64_t* full_bar,
+                                              uint64_t* empty_bar, uint8_t* smem) {
+    using G = TileGeom<TH, R>;
+    constexpr int NB = G::NBUF;
+    const int n_items = cv.h->n_items;
+    int claimed = atomicAdd(counter, 1);
+    for (int t = 0;; ++t) {
+        const int b = t % NB;
+        const int it = claimed;
+        if (it < n_items) claimed = atomicAdd(counter, 1);
+        if (t >= NB && !mbar_wait_bounded(&empty_bar[b], ((t / NB) - 1) & 1, kWaitLimitNs)) {
+            atomicOr(status, kStatusTimeout);
+            return;
+        }
+        ItemInfo& in = info[b];
+        in.id = it;
+        if (it >= n_items) {
+            mbar_arrive(&full_bar[b]);
+            return;
+        }
+        const Item wi = decode_item(cv, tiles, it);
+        const FrameDesc& fd = cv.fds[wi.frame];
+        in.level = wi.level;
+        in.x0 = wi.tx * G::TW;
+        in.y0 = wi.ty * TH;
+        in.wk = fd.w >> wi.level;
+        in.hk = fd.h >> wi.level;
+        in.gw = fd.gw;
+        in.keys = fd.keys;
+        const CUtensorMap* map =
+            wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
+        fence_tensormap_acquire(map);
+        mbar_arrive_expect_tx(&full_bar[b], G::BOX);
+        tma_load_2d(smem + G::IMG_OFF + b * G::BOXA, map, &full_bar[b], (in.x0 - 8) & ~15, in.y0 - R - 3);
+    }
+}
+
 template <int TH, int MODE, int R = 1>
 __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_t* __restrict__ call,
                                                                  int32_t* __restrict__ counter,
@@ -567,40 +611,8 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
     __syncthreads();
 
     if (warp == kConsumers / 32) {
-        // ---- producer warp: claims items, fills the ring, runs ahead ----
-        if (lane == 0) {
-            const int32_t* tiles = cached ? tiles_sh : cv.tiles;
-            int claimed = atomicAdd(counter, 1);  // claimed one item ahead of its use
-            for (int t = 0;; ++t) {
-                const int b = t % NB;
-                const int it = claimed;
-                if (it < n_items) claimed = atomicAdd(counter, 1);
-                if (t >= NB && !mbar_wait_bounded(&empty_bar[b], ((t / NB) - 1) & 1, kWaitLimitNs)) {
-                    atomicOr(status, kStatusTimeout);
-                    break;
-                }
-                ItemInfo& in = info[b];
-                in.id = it;
-                if (it >= n_items) {  // tell the consumers to stop
-                    mbar_arrive(&full_bar[b]);
-                    break;
-                }
-                const Item wi = decode_item(cv, tiles, it);
-                const FrameDesc& fd = cv.fds[wi.frame];
-                in.level = wi.level;
-                in.x0 = wi.tx * G::TW;
-                in.y0 = wi.ty * TH;
-                in.wk = fd.w >> wi.level;
-                in.hk = fd.h >> wi.level;
-                in.gw = fd.gw;
-                in.keys = fd.keys;
-                const CUtensorMap* map =
-                    wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
-                fence_tensormap_acquire(map);
-                mbar_arrive_expect_tx(&full_bar[b], G::BOX);
-                tma_load_2d(smem + G::IMG_OFF + b * G::BOXA, map, &full_bar[b], (in.x0 - 8) & ~15, in.y0 - R - 3);
-            }
-        }
+        if (lane == 0) produce_tiles<TH, R>(cv, cached ? tiles_sh : cv.tiles, counter, status, info, full_bar, empty_bar,
+                                            smem);
         return;
     }
 

@@ -94,40 +94,8 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
     __syncthreads();
 
     if (warp == kConsumers / 32) {
-        // ---- producer warp: claims items, fills the ring, runs ahead ----
-        if (lane == 0) {
-            const int32_t* tiles = cached ? tiles_sh : cv.tiles;
-            int claimed = atomicAdd(counter, 1);
-            for (int t = 0;; ++t) {
-                const int b = t % NB;
-                const int it = claimed;
-                if (it < n_items) claimed = atomicAdd(counter, 1);
-                if (t >= NB && !mbar_wait_bounded(&empty_bar[b], ((t / NB) - 1) & 1, kWaitLimitNs)) {
-                    atomicOr(status, kStatusTimeout);
-                    break;
-                }
-                ItemInfo& in = info[b];
-                in.id = it;
-                if (it >= n_items) {
-                    mbar_arrive(&full_bar[b]);
-                    break;
-                }
-                const Item wi = decode_item(cv, tiles, it);
-                const FrameDesc& fd = cv.fds[wi.frame];
-                in.level = wi.level;
-                in.x0 = wi.tx * G::TW;
-                in.y0 = wi.ty * TH;
-                in.wk = fd.w >> wi.level;
-                in.hk = fd.h >> wi.level;
-                in.gw = fd.gw;
-                in.keys = fd.keys;
-                const CUtensorMap* map =
-                    wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
-                fence_tensormap_acquire(map);
-                mbar_arrive_expect_tx(&full_bar[b], G::BOX);
-                tma_load_2d(smem + G::IMG_OFF + b * G::BOXA, map, &full_bar[b], (in.x0 - 8) & ~15, in.y0 - 4);
-            }
-        }
+        if (lane == 0) produce_tiles<TH, 1>(cv, cached ? tiles_sh : cv.tiles, counter, status, info, full_bar, empty_bar,
+                                            smem);
         return;
     }
 
