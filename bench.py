@@ -146,21 +146,28 @@ def kernel_source_hash(kernel: str = "fast_nms_cell") -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str, kernel: str = "fast_nms_cell"):
-    """dram bytes per launch of a detect kernel from its committed ncu
-    summary (profiles/<kernel>_<workload>.md), if it was taken on the current
-    kernel source; else None."""
+def recorded_profile(workload: str, kernel: str = "fast_nms_cell") -> dict:
+    """Figures of a detect kernel's committed ncu summary
+    (profiles/<kernel>_<workload>.md: `key: value` lines), if it was taken on
+    the current kernel source; else {}."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
-        return None
-    src = traffic = None
+        return {}
+    vals = {}
     with open(path) as f:
         for line in f:
-            if line.startswith("kernel_source_sha256:"):
-                src = line.split(":", 1)[1].split()[0].strip()
-            if line.startswith("dram_bytes_per_launch:"):
-                traffic = float(line.split(":", 1)[1].strip())
-    return traffic if src == kernel_source_hash(kernel) else None
+            for key in ("kernel_source_sha256", "dram_bytes_per_launch", "alu_pipe_pct", "issue_active_pct"):
+                if line.startswith(key + ":"):
+                    vals[key] = line.split(":", 1)[1].split()[0].strip()
+    if vals.get("kernel_source_sha256") != kernel_source_hash(kernel):
+        return {}
+    return vals
+
+
+def recorded_traffic(workload: str, kernel: str = "fast_nms_cell"):
+    """dram bytes per launch from the committed ncu summary, or None."""
+    v = recorded_profile(workload, kernel).get("dram_bytes_per_launch")
+    return float(v) if v is not None else None
 
 
 def max_over_ranks(value: float) -> float:
@@ -407,6 +414,12 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
                        "frac": round(achieved / peak, 4), "traffic": traffic,
                        "kernel": kname, "peak_kind": f"{kind} hbm_gbs",
                        "algorithmic_bytes_per_launch": int(fused_bytes)}
+    prof_vals = recorded_profile(args.workload, kname.replace("_kernel", ""))
+    if "alu_pipe_pct" in prof_vals:
+        # what binds instead: integer issue (ncu on the same kernel source)
+        out["roofline"]["alu"] = {"pipe_alu_pct": float(prof_vals["alu_pipe_pct"]),
+                                  "issue_active_pct": float(prof_vals["issue_active_pct"]),
+                                  "source": f"profiles/{kname.replace('_kernel', '')}_{args.workload}.md"}
     out["stage_ms"] = {"pyramid": round(stage[0], 5), kname.replace("_kernel", ""): round(stage[1], 5),
                        "decode": round(stage[2], 5)}
     step_gbs = step_bytes / (ms_per_step * 1e-3) / 1e9
