@@ -140,6 +140,71 @@ def test_large_frames_sampled(dets):
             assert_parity(got, cnt, check, thresh, arc, 64, 4, 0)
 
 
+def cells_from_oracle_crop(img, ox, oy, cw, ch, thresh, arc, cell, levels, mode=0):
+    """Records of the cells [ox, ox + cw) x [oy, oy + ch) (level-0 pixels, on
+    the cell grid) of a frame too large for the oracle, computed by the oracle
+    on a crop: every level's score map and 3x3 NMS on the crop's pyramid, then
+    the cell maxima (highest score, then lower level, y, x) over the
+    survivors inside each cell.  The crop starts 4 pixels of the coarsest
+    level before the cells (aligned to 2^(levels-1)) and ends as far after
+    them, so the circle and NMS context of every pixel in the cells is in it."""
+    h, w = img.shape
+    a = 1 << (levels - 1)
+    m = 4 * a
+    x0, y0 = max(0, ox - m), max(0, oy - m)
+    x1, y1 = min(w, ox + cw + m), min(h, oy + ch + m)
+    x1 = x0 + (x1 - x0) // a * a if x1 < w else x1
+    y1 = y0 + (y1 - y0) // a * a if y1 < h else y1
+    crop = np.ascontiguousarray(img[y0:y1, x0:x1])
+    gx, gy = (cw + cell - 1) // cell, (ch + cell - 1) // cell
+    best = {}
+    for k, lev in enumerate(oracle.pyramid(crop, levels)):
+        surv = oracle.nms(oracle.score_map(lev, thresh, arc, mode), 1)
+        ys, xs = np.nonzero(surv)
+        for yk, xk in zip(ys, xs):
+            X, Y = ((int(xk) + (x0 >> k)) << k), ((int(yk) + (y0 >> k)) << k)
+            if not (ox <= X < ox + cw and oy <= Y < oy + ch):
+                continue
+            cid = ((Y - oy) // cell) * gx + (X - ox) // cell
+            key = (int(surv[yk, xk]), -k, -(int(yk) + (y0 >> k)), -(int(xk) + (x0 >> k)))
+            if cid not in best or key > best[cid][0]:
+                best[cid] = (key, (X, Y, k, int(surv[yk, xk])))
+    out = np.tile(np.array([-1, -1, -1, 0], np.int32), (gx * gy, 1))
+    for cid, (_, rec) in best.items():
+        out[cid] = rec
+    return out
+
+
+def test_maximum_frame_size_sampled(dets):
+    """The largest frame the ABI takes (w * h just below 2^28), 3 levels, 64x64
+    cells: 16 blocks of 3x3 cells (corners, edges, interior) against the
+    oracle on crops; the next larger frame is rejected."""
+    base = synth.make_frame(2048, 2048, seed=123, n_shapes=60)
+    W, H = 16384, 16383
+    img = np.ascontiguousarray(np.tile(base, (8, 8))[:H, :W])
+    frame = to_gpu(img)
+    outs, counts = dets[0].detect([frame], 15, 9, 64, 3)
+    dets[0].sync()
+    got = outs[0].cpu().numpy()
+    gw = (W + 63) // 64
+    gh = (H + 63) // 64
+    rng = np.random.default_rng(3)
+    blocks = [(0, 0), (gw - 3, 0), (0, gh - 3), (gw - 3, gh - 3)]
+    blocks += [(int(rng.integers(0, gw - 3)), int(rng.integers(0, gh - 3))) for _ in range(12)]
+    for bx, by in blocks:
+        ox, oy = bx * 64, by * 64
+        cw, ch = min(3 * 64, W - ox), min(3 * 64, H - oy)
+        want = cells_from_oracle_crop(img, ox, oy, cw, ch, 15, 9, 64, 3)
+        ncx = (cw + 63) // 64
+        for j in range((ch + 63) // 64):
+            for i in range(ncx):
+                assert np.array_equal(got[(by + j) * gw + bx + i], want[j * ncx + i]), (bx + i, by + j)
+    assert counts.cpu().numpy()[0] == int((got[:, 2] >= 0).sum())
+    too_big = torch.zeros((16384, 16384), dtype=torch.uint8, device="cuda")
+    with pytest.raises(vio.VioError):
+        dets[0].detect([too_big], 15, 9, 64, 3)
+
+
 # ---- edge cases -------------------------------------------------------------
 
 EDGE_SIZES = [(7, 7, 1), (8, 7, 1), (13, 9, 1), (31, 17, 1), (100, 37, 2), (257, 131, 3),
