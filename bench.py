@@ -138,11 +138,18 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_hash(kernel: str = "fast_nms_cell") -> str:
-    """Hash of the sources a detect kernel is compiled from."""
+    """Hash of the code a detect kernel is compiled from: its sources with
+    comments and blank space removed, so that edits of comments alone keep
+    a recorded profile valid."""
+    import re
+
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, "paper_2003_13493_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2003_13493_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

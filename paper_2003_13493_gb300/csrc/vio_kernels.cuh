@@ -1,5 +1,6 @@
-// Device code: pyramid half-sampling, the fused FAST + 3x3 NMS + cell-max
-// kernel, and the cell decode.  All arithmetic is integer.
+// Device code: pyramid half-sampling, the fused FAST + NMS + cell-max kernel
+// (3x3 to 9x9 NMS windows, scores SAD-B / SAD-A / MT), and the cell decode.
+// All arithmetic is integer.
 #pragma once
 #include <cuda.h>
 #include <stdint.h>
@@ -407,8 +408,9 @@ __device__ __forceinline__ uint32_t coarse4(uint32_t C, uint32_t L, uint32_t R, 
 //   2. Coarse test on every score-region pixel, 8 pixels per lane, pixels
 //      outside the testable area masked off; each warp appends the kept
 //      pixels of each of its row pairs to its own queue (warp scan).
-//   3. Each warp runs the full segment test and score on its queue, writes
-//      scores into the score tile and compacts the corners in place.
+//   3. Each warp runs the full segment test on its queue and compacts the
+//      corners in place, then scores the corners and writes the scores into
+//      the score tile.
 //   4. After a barrier of the consumer warps (NMS reads other warps' rows),
 //      (2R+1)x(2R+1) NMS on the corner lists; when a warp's survivors share one cell
 //      their packed keys are max-reduced with __reduce_max_sync and folded
