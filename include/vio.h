@@ -215,7 +215,9 @@ vio_status vio_detect_host_async(vio_ctx* ctx, const uint8_t* const* host_frames
 vio_status vio_stage_ms(vio_ctx* ctx, float* ms3);
 
 /* Waits for all work the context enqueued on `stream` and reports any
- * device-side status (VIO_ERR_TIMEOUT when a bounded wait gave up). */
+ * device-side status: VIO_ERR_TIMEOUT when a bounded wait gave up,
+ * VIO_ERR_CUDA when the decode found a cell key that does not lie in its
+ * cell (corrupted keys).  The status word is cleared. */
 vio_status vio_sync(vio_ctx* ctx, vio_stream stream);
 
 /* Diagnostic of the failure path: runs one warp that waits, with the same

@@ -97,6 +97,15 @@ const void* device_alias(const void* host) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// Reads and clears the device status word after a synchronisation.
+vio_status take_status(vio_ctx* ctx) {
+    const uint32_t bits = *ctx->h_status;
+    if (!bits) return VIO_OK;
+    *ctx->h_status = 0;
+    if (bits & kStatusTimeout) return fail(ctx, VIO_ERR_TIMEOUT, "a bounded device-side wait timed out");
+    return fail(ctx, VIO_ERR_CUDA, "a decoded feature lies outside its cell (corrupted cell keys)");
+}
+
 vio_status encode_map(vio_ctx* ctx, CUtensorMap* out, const void* ptr, int w, int h, int pitch, int bw, int bh) {
     MapKey key{(uintptr_t)ptr, w, h, pitch, bw, bh};
     auto it = ctx->map_cache.find(key);
@@ -327,6 +336,7 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
     hdr->off_tiles = (uint32_t)off_tiles;
     hdr->off_blocks = (uint32_t)off_blocks;
     hdr->off_cells = (uint32_t)off_cells;
+    hdr->status = ctx->d_status;
     for (int k = 0; k < levels; ++k) {
         const uint64_t d = (uint64_t)(cell >> k);  // >= 2: cell is a multiple of 32, k <= 4
         hdr->cell_magic[k] = (uint32_t)(((1ull << 32) + d - 1) / d);
@@ -674,6 +684,7 @@ vio_status vio_destroy(vio_ctx* ctx) {
 vio_status vio_detect(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims* dims, int n, int thresh,
                       int arc, int cell, int levels, vio_feature* const* out_cells, int32_t* out_counts,
                       vio_stream stream) {
+    NvtxRange nvtx("vio_detect");
     vio_status st = check_args(ctx, frames, dims, n, thresh, arc, cell, levels, out_cells);
     if (st != VIO_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -712,6 +723,7 @@ vio_status vio_detect(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims
 vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims* dims, int n,
                             const int* thresholds, const int* arc_lens, int n_params, int cell, int levels,
                             vio_feature* const* out_cells, int32_t* out_counts, vio_stream stream) {
+    NvtxRange nvtx("vio_detect_sweep");
     if (!ctx) return VIO_ERR_INVALID_ARG;
     if (!thresholds || !arc_lens || n_params < 1 || n_params > 64)
         return fail(ctx, VIO_ERR_INVALID_ARG, "n_params must be in 1..64 with thresholds and arc lengths");
@@ -800,6 +812,7 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
 vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims, int n, int thresh,
                            int arc, int cell, int levels, vio_feature* const* host_cells, int32_t* host_counts,
                            vio_stream stream) {
+    NvtxRange nvtx("vio_detect_host");
     vio_status st = check_args(ctx, host_frames, dims, n, thresh, arc, cell, levels, host_cells);
     if (st != VIO_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -842,10 +855,7 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
     else
         VIO_CK(cudaMemcpyAsync(ctx->h_out, ctx->d_cells, cell_bytes, cudaMemcpyDeviceToHost, s));
     VIO_CK(cudaStreamSynchronize(s));
-    if (*ctx->h_status) {
-        *ctx->h_status = 0;
-        return fail(ctx, VIO_ERR_TIMEOUT, "a bounded device-side wait timed out");
-    }
+    if ((st = take_status(ctx)) != VIO_OK) return st;
     const int4* rec = reinterpret_cast<const int4*>(ctx->h_out);
     for (int i = 0; i < n; ++i)
         if (!direct_out[i])
@@ -858,6 +868,7 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
 vio_status vio_detect_host_async(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims, int n,
                                  int thresh, int arc, int cell, int levels, vio_feature* const* host_cells,
                                  int32_t* host_counts, vio_stream stream) {
+    NvtxRange nvtx("vio_detect_host_async");
     vio_status st = check_args(ctx, host_frames, dims, n, thresh, arc, cell, levels, host_cells);
     if (st != VIO_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -913,11 +924,7 @@ vio_status vio_sync(vio_ctx* ctx, vio_stream stream) {
     if (!ctx) return VIO_ERR_INVALID_ARG;
     VIO_CK(cudaSetDevice(ctx->cfg.device));
     VIO_CK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
-    if (*ctx->h_status) {
-        *ctx->h_status = 0;
-        return fail(ctx, VIO_ERR_TIMEOUT, "a bounded device-side wait timed out");
-    }
-    return VIO_OK;
+    return take_status(ctx);
 }
 
 vio_status vio_selftest_timeout(vio_ctx* ctx, uint32_t limit_us) {
@@ -930,10 +937,8 @@ vio_status vio_selftest_timeout(vio_ctx* ctx, uint32_t limit_us) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (e != cudaSuccess) return fail(ctx, VIO_ERR_CUDA, std::string("selftest: ") + cudaGetErrorString(e));
-    if (*ctx->h_status) {
-        *ctx->h_status = 0;
-        return fail(ctx, VIO_ERR_TIMEOUT, "a bounded device-side wait timed out");
-    }
+    const vio_status st = take_status(ctx);
+    if (st != VIO_OK) return st;
     return fail(ctx, VIO_ERR_CUDA, "selftest: the bounded wait did not report its timeout");
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <string>
@@ -46,6 +47,15 @@ struct MapHash {
     }
 };
 
+
+// A named range on the profiler's timeline for the duration of a scope (NVTX;
+// free when no profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // One input slot of vio_detect_host_async: frames of one call in flight.
 struct HostSlot {

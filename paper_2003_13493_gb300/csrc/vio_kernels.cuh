@@ -10,7 +10,8 @@
 namespace vio {
 
 constexpr int kMaxLevels = 5;
-constexpr uint32_t kStatusTimeout = 1u;
+constexpr uint32_t kStatusTimeout = 1u;  // a bounded wait gave up
+constexpr uint32_t kStatusBadKey = 2u;   // a decoded cell key lies outside its cell
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per bounded wait
 
 // Per-frame descriptor, rewritten by the host for every call.
@@ -46,7 +47,7 @@ struct CallHeader {
     // x < 2^16, umulhi(x, magic) == x / (cell >> k) == (x << k) / cell exactly
     uint32_t cell_magic[kMaxLevels];
     int32_t n_cells;       // cells of all frames
-    uint64_t pad1;
+    uint32_t* status;      // device-visible status word for the decode's checks, or nullptr
 };
 
 struct CallView {
@@ -777,6 +778,12 @@ static __global__ void __launch_bounds__(256) decode_kernel(const uint8_t* __res
                 rec = make_int4(x << k, y << k, k, (int)(key >> 32));
                 fd.keys[c] = 0;
                 hit = true;
+                // consistency of the packed key with the cell it was folded into
+                const uint32_t magic = cv.h->cell_magic[0];
+                if (cv.h->status && (k >= cv.h->levels || rec.x >= fd.w || rec.y >= fd.h ||
+                                     __umulhi((uint32_t)rec.y, magic) * (uint32_t)fd.gw +
+                                             __umulhi((uint32_t)rec.x, magic) != (uint32_t)c))
+                    atomicOr(cv.h->status, kStatusBadKey);
             }
             fd.out[c] = rec;
         }

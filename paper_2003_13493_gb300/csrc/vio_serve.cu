@@ -128,6 +128,7 @@ vio_status grow_host(uint8_t** p, size_t* cap, size_t need) {
 // pyramid kernel through their device mapping, records are written straight
 // into the lane's pinned result buffer, then the counts follow.
 vio_status launch_lane(vio_server_state* S, Lane& L) {
+    vio::NvtxRange nvtx("vio_serve_batch");
     const auto& c = S->cfg;
     const int n = (int)L.batch.size();
     size_t cell_need = 0;
@@ -171,6 +172,13 @@ vio_status launch_lane(vio_server_state* S, Lane& L) {
 void finish_lane(vio_server_state* S, Lane& L) {
     const int n = (int)L.batch.size();
     const uint64_t t = now_ns();
+    // the batch is complete; a device-side status of the lane stops serving
+    const vio_status dst = vio_sync(L.ctx, reinterpret_cast<vio_stream>(L.stream));
+    if (dst != VIO_OK) {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->error = dst;
+        S->stop = true;
+    }
     size_t cell_total = 0;
     for (auto& r : L.batch) cell_total += r.ncell;
     const int32_t* counts = reinterpret_cast<const int32_t*>(L.h_cells + cell_total * sizeof(vio_feature));

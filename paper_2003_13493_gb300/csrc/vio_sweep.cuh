@@ -270,6 +270,11 @@ static __global__ void __launch_bounds__(256) sweep_decode_kernel(const uint8_t*
                 rec = make_int4(x << k, y << k, k, (int)(key >> 32));
                 *kp = 0;
                 hit = true;
+                const uint32_t magic = cv.h->cell_magic[0];
+                if (cv.h->status && (k >= cv.h->levels || rec.x >= fd.w || rec.y >= fd.h ||
+                                     __umulhi((uint32_t)rec.y, magic) * (uint32_t)fd.gw +
+                                             __umulhi((uint32_t)rec.x, magic) != (uint32_t)c))
+                    atomicOr(cv.h->status, kStatusBadKey);
             }
             sw->outs[s * nf + f][c] = rec;
             g = s * nf + f;

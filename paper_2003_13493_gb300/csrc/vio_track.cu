@@ -82,6 +82,7 @@ void vio_track_params_default(vio_track_params* p) {
 vio_status vio_track(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* const* next, const vio_dims* dims,
                      int n_pairs, const float* const* pts, const int* n_pts, const vio_track_params* params,
                      vio_track_result* const* out, vio_stream stream) {
+    NvtxRange nvtx("vio_track");
     if (!ctx) return VIO_ERR_INVALID_ARG;
     vio_track_params p;
     if (params) p = *params; else vio_track_params_default(&p);
