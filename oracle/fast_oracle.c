@@ -27,13 +27,14 @@
  *                    (one grid for all levels, level-k positions scaled
  *                    up by 2^k).
  *
- * Readings where the paper is silent (all stated again in the design doc):
+ * Readings where the paper is silent:
  *   - circle order: clockwise from the top point (0,-3);
  *   - SAD-B sums |I_x - I_center| over all 16 points, SAD-A over the
  *     maximal homogeneous run that makes the point a corner;
  *   - MT is the largest t in [eps, 255] at which the point is a corner;
- *   - NMS keeps a pixel when its score is > 0 and >= each of its 8
- *     neighbours (pixels outside the level count as 0);
+ *   - NMS keeps a pixel when its score is > 0 and >= each of its
+ *     (2n+1)^2 - 1 neighbours, n = 1 (3x3) unless asked otherwise (pixels
+ *     outside the level count as 0);
  *   - cell winner: highest score, then lower level, then lower y, then
  *     lower x (all in level coordinates); position reported as
  *     (x << k, y << k); an empty cell is (-1, -1, -1, 0);
