@@ -126,3 +126,33 @@ def test_lanes_inherit_score_and_nms_radius(pool):
         assert np.array_equal(cells, ref) and cnt == n
     det.serve_stop()
     det.close()
+
+
+def test_pinned_and_pageable_frames_in_one_mix(pool):
+    """Pinned frames are read by the lanes' pyramid kernels through their
+    device mapping, pageable or misaligned ones are copied; results must not
+    depend on where a frame lives."""
+    keep = []
+    frames = []
+    for k, (sid, f) in enumerate(pool):
+        if k % 3 == 0:
+            frames.append((sid, f))
+            continue
+        off = 0 if k % 3 == 1 else 1  # aligned / misaligned pinned
+        buf = torch.empty(f.size + off + 64, dtype=torch.uint8).pin_memory()
+        v = buf.numpy()[off:off + f.size].reshape(f.shape)
+        v[...] = f
+        keep.append(buf)
+        frames.append((sid, v))
+    det = vio.Detector(max_frames=32)
+    det.serve_start(max_batch=5, lanes=3, **PARAMS)
+    tickets = [(det.submit(sid, f), f) for sid, f in frames * 2]
+    det.drain(60000)
+    for t, f in tickets:
+        done, cells, cnt = det.poll(t, f.shape[1], f.shape[0])
+        assert done
+        ref, n = oracle.detect(np.ascontiguousarray(f), PARAMS["thresh"], PARAMS["arc_len"], PARAMS["cell_size"],
+                               PARAMS["levels"])
+        assert np.array_equal(cells, ref) and cnt == n
+    det.serve_stop()
+    det.close()
