@@ -103,6 +103,7 @@ vio_status take_status(vio_ctx* ctx) {
     if (!bits) return VIO_OK;
     *ctx->h_status = 0;
     if (bits & kStatusTimeout) return fail(ctx, VIO_ERR_TIMEOUT, "a bounded device-side wait timed out");
+    if (bits & kStatusBounds) return fail(ctx, VIO_ERR_CUDA, "a device-side index check failed (checked build)");
     return fail(ctx, VIO_ERR_CUDA, "a decoded feature lies outside its cell (corrupted cell keys)");
 }
 

@@ -12,6 +12,21 @@ namespace vio {
 constexpr int kMaxLevels = 5;
 constexpr uint32_t kStatusTimeout = 1u;  // a bounded wait gave up
 constexpr uint32_t kStatusBadKey = 2u;   // a decoded cell key lies outside its cell
+constexpr uint32_t kStatusBounds = 4u;   // checked build: an index left its buffer
+
+// Index checks of the checked build (compiled with -DVIO_CHECKED): a failed
+// check records kStatusBounds and the access is skipped.  In the normal
+// build every check is `true` and compiles away.
+__device__ __forceinline__ bool vio_guard(bool in_bounds, uint32_t* status) {
+#ifdef VIO_CHECKED
+    if (!in_bounds && status) atomicOr(status, kStatusBounds);
+    return in_bounds;
+#else
+    (void)in_bounds;
+    (void)status;
+    return true;
+#endif
+}
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per bounded wait
 
 // Per-frame descriptor, rewritten by the host for every call.
@@ -455,7 +470,7 @@ struct Item {
 struct ItemInfo {
     int32_t id;            // item index; >= n_items ends the consumers' loop
     int32_t level, x0, y0;
-    int32_t wk, hk, gw, pad;
+    int32_t wk, hk, gw, gh;
     uint64_t* keys;
 };
 
@@ -486,7 +501,7 @@ __device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x002
 template <bool HIGH_T, bool THREE, int TH, int R>
 __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* queue, int xw, uint32_t k7,
                                                   int warp, int lane, int row_lo, int row_hi, uint32_t vm0,
-                                                  uint32_t vm1) {
+                                                  uint32_t vm1, uint32_t* status = nullptr) {
     using G = TileGeom<TH, R>;
     constexpr int RW = G::BW / 4;
     constexpr int NW = (G::PPW + 3) / 4;  // mask words per lane
@@ -525,7 +540,9 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
         while (mw) {
             const int b = 31 - __clz(mw);
             mw ^= 1u << b;
-            queue[pos++] = (uint16_t)(base + (4 * w + (b >> 3)) * (2 * G::SW) + (b & 7));
+            const int e = base + (4 * w + (b >> 3)) * (2 * G::SW) + (b & 7);
+            if (vio_guard(pos < G::QCAP && e < G::SR * G::SW, status)) queue[pos] = (uint16_t)e;
+            ++pos;
         }
     }
     return __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -566,6 +583,7 @@ __device__ __forceinline__ void produce_tiles(const CallView& cv, const int32_t*
         in.wk = fd.w >> wi.level;
         in.hk = fd.h >> wi.level;
         in.gw = fd.gw;
+        in.gh = fd.gh;
         in.keys = fd.keys;
         const CUtensorMap* map =
             wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
@@ -659,11 +677,11 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             (void)lx;
             const int xw = xoff / 4;
             if (high_t) {
-                total = three ? coarse_and_compact<true, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1)
-                              : coarse_and_compact<true, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1);
+                total = three ? coarse_and_compact<true, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status)
+                              : coarse_and_compact<true, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status);
             } else {
-                total = three ? coarse_and_compact<false, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1)
-                              : coarse_and_compact<false, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1);
+                total = three ? coarse_and_compact<false, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status)
+                              : coarse_and_compact<false, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status);
             }
         }
         __syncwarp();
@@ -675,11 +693,12 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             const int e = e0 + lane;
             uint32_t s = 0;
             int idx = 0;
-            if (e < total) {
+            if (e < total && vio_guard(e < G::QCAP, status)) {
                 idx = queue[e];
                 // box offset of score-region pixel (idx >> 7, idx & 127); the
                 // score is taken below, on the compacted corners only
-                s = eval_corner<MODE, G::BW, false>(img_base + idx + 16 * (idx >> 7), thresh, n_arc);
+                if (vio_guard(idx < G::SR * G::SW, status))
+                    s = eval_corner<MODE, G::BW, false>(img_base + idx + 16 * (idx >> 7), thresh, n_arc);
             }
             const uint32_t cm = __ballot_sync(0xFFFFFFFFu, s != 0);
             if (s) queue[ncorner + __popc(cm & lt_mask)] = (uint16_t)idx;
@@ -718,9 +737,12 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
                             if (dy != 0 || dx != 0) keep &= s >= q[dy * G::SW + dx];
                     if (keep) {
                         const uint32_t x = (uint32_t)(x0 - 4 + scx), y = (uint32_t)(y0 - R + sr);
-                        cell_id = __umulhi(y, magic) * (uint32_t)in.gw + __umulhi(x, magic);
-                        hi = s;
-                        lo = 0xFFFFFFFFu - (((uint32_t)k << 28) | (y * (uint32_t)Wk + x));
+                        const uint32_t cx = __umulhi(x, magic), cy = __umulhi(y, magic);
+                        if (vio_guard(cx < (uint32_t)in.gw && cy < (uint32_t)in.gh, status)) {
+                            cell_id = cy * (uint32_t)in.gw + cx;
+                            hi = s;
+                            lo = 0xFFFFFFFFu - (((uint32_t)k << 28) | (y * (uint32_t)Wk + x));
+                        }
                     }
                 }
             }

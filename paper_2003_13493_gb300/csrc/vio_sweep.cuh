@@ -135,9 +135,9 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             }
             const int xw = xoff / 4;
             total = high_t ? coarse_and_compact<true, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo, row_hi,
-                                                                     vm0, vm1)
+                                                                     vm0, vm1, status)
                            : coarse_and_compact<false, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo, row_hi,
-                                                                      vm0, vm1);
+                                                                      vm0, vm1, status);
         }
         __syncwarp();
 
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             const int e = e0 + lane;
             uint32_t cmask = 0;
             int idx = 0;
-            if (e < total) {
+            if (e < total && vio_guard(e < G::QCAP && queue[e] < G::SR * G::SW, status)) {
                 idx = queue[e];
                 const uint8_t* p = img_base + idx + 16 * (idx >> 7);
                 const uint32_t c = p[0];
@@ -206,9 +206,14 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
                     keep = qm[0] & allowed;
                     if (keep) {
                         const uint32_t x = (uint32_t)(x0 - 4 + scx), y = (uint32_t)(y0 - 1 + sr);
-                        cell_id = __umulhi(y, magic) * (uint32_t)in.gw + __umulhi(x, magic);
-                        hi = s;
-                        lo = 0xFFFFFFFFu - (((uint32_t)k << 28) | (y * (uint32_t)Wk + x));
+                        const uint32_t cx = __umulhi(x, magic), cy = __umulhi(y, magic);
+                        if (vio_guard(cx < (uint32_t)in.gw && cy < (uint32_t)in.gh, status)) {
+                            cell_id = cy * (uint32_t)in.gw + cx;
+                            hi = s;
+                            lo = 0xFFFFFFFFu - (((uint32_t)k << 28) | (y * (uint32_t)Wk + x));
+                        } else {
+                            keep = 0;
+                        }
                     }
                 }
             }

@@ -79,17 +79,21 @@ def header_functions() -> list[str]:
 
 
 def lib_path() -> str:
-    return _build.LIB_PATH
+    """Path of the library load() uses (the checked build with VIO_CHECKED=1)."""
+    return _build.CHECKED_LIB_PATH if os.environ.get("VIO_CHECKED") == "1" else _build.LIB_PATH
 
 
 def load(build_if_missing: bool = True):
-    """Loads the library (building it first if asked and needed)."""
+    """Loads the library (building it first if asked and needed).  With
+    VIO_CHECKED=1 in the environment the checked build (device-side index
+    checks enabled) is loaded instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB_PATH
+    checked = os.environ.get("VIO_CHECKED") == "1"
+    path = lib_path()
     if build_if_missing:
-        path = _build.build()
+        path = _build.build(checked=checked)
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path}")
     lib = ctypes.CDLL(path)
