@@ -73,22 +73,24 @@ __device__ __forceinline__ bool cholesky4(float (&A)[4][4]) {
     return true;
 }
 
-// Solves L L^T x = b with the factor from cholesky4.
-__device__ __forceinline__ void chol_solve4(const float (&L)[4][4], const float (&b)[4], float (&x)[4]) {
+// Solves L L^T x = b with the factor from cholesky4 and the reciprocals of
+// its diagonal (computed once per level: the iterations then multiply).
+__device__ __forceinline__ void chol_solve4(const float (&L)[4][4], const float (&inv)[4], const float (&b)[4],
+                                            float (&x)[4]) {
     float y[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float s = b[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-        y[i] = s / L[i][i];
+        y[i] = s * inv[i];
     }
 #pragma unroll
     for (int i = 3; i >= 0; --i) {
         float s = y[i];
 #pragma unroll
         for (int k = i + 1; k < 4; ++k) s -= L[k][i] * x[k];
-        x[i] = s / L[i][i];
+        x[i] = s * inv[i];
     }
 }
 
@@ -163,12 +165,18 @@ __device__ bool track_level(const TrackLevel& lv, float cx, float cy, float* tg,
     L[3][3] = use_off ? warp_sum(h33) : 1.f;
     L[0][1] = L[0][2] = L[0][3] = L[1][2] = L[1][3] = L[2][3] = 0.f;
     if (!cholesky4(L)) return false;
+    const float inv[4] = {1.f / L[0][0], 1.f / L[1][1], 1.f / L[2][2], 1.f / L[3][3]};
+    const float min2 = min_update * min_update;
+    float rr_last = -1.f;  // squared residual sum of the latest iteration
 
     for (int it = 0; it < max_iters; ++it) {
         // this lane's samples: column xs, rows ys .. ys + NPX - 1 of the next image
         const float xs = o0 + (float)col + tx, ys = o1 + (float)row0 + ty;
         ok = inside(xs, ys, lv.w, lv.h) && inside(xs, ys + (float)(NPX - 1), lv.w, lv.h);
-        if (!__all_sync(0xFFFFFFFFu, ok)) return false;
+        if (!__all_sync(0xFFFFFFFFu, ok)) {
+            if (rr_last >= 0.f) residual = sqrtf(rr_last * (1.f / (P * P)));
+            return false;
+        }
         const float fx = floorf(xs), fy = floorf(ys);
         const float ax = xs - fx, ay = ys - fy;
         const uint8_t* q = lv.next + (size_t)(int)fy * lv.pitch_next + (int)fx;
@@ -187,16 +195,20 @@ __device__ bool track_level(const TrackLevel& lv, float cx, float cy, float* tg,
             rr = fmaf(r, r, rr);
         }
         const float b[4] = {warp_sum(b0), warp_sum(b1), use_gain ? warp_sum(b2) : 0.f, use_off ? warp_sum(b3) : 0.f};
-        residual = sqrtf(warp_sum(rr) * (1.f / (P * P)));
+        rr_last = warp_sum(rr);
         float dq[4];
-        chol_solve4(L, b, dq);
+        chol_solve4(L, inv, b, dq);
         tx -= dq[0];
         ty -= dq[1];
         alpha += dq[2];
         beta += dq[3];
         ++iters;
-        if (sqrtf(dq[0] * dq[0] + dq[1] * dq[1]) < min_update) break;
+        if (dq[0] * dq[0] + dq[1] * dq[1] < min2) {
+            residual = sqrtf(rr_last * (1.f / (P * P)));
+            return true;
+        }
     }
+    if (rr_last >= 0.f) residual = sqrtf(rr_last * (1.f / (P * P)));
     return true;
 }
 
