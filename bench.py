@@ -370,11 +370,83 @@ def run_ours(args, rank, world, local_rank):
     }
     if sweep:
         res["detections_per_s"] = round(world * n * npar * args.steps / (ms / 1e3), 1)
+    if not args.no_extras and not sweep:
+        res["e2e"] = e2e_leg(args, wl, det, dev, stream, frames_np, dims, n, world)
     if rank == 0 and not args.no_extras:
         res.update(extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cptr, n, mpx,
                           ms_per_step))
     det.close()
     return res
+
+
+def e2e_leg(args, wl, det, dev, stream, frames_np, dims, n, world) -> dict:
+    """End to end through the host-buffer entry points (pinned host frames and
+    outputs): each step copies its frames in and its records out.  Every rank
+    runs it on its own GPU; the whole-job rate divides all ranks' frames by
+    the slowest rank's time."""
+    import torch
+
+    from paper_2003_13493_gb300 import vio
+
+    pinned = [torch.from_numpy(f).pin_memory() for f in frames_np]
+    host_frames = [p.numpy() for p in pinned]
+
+    def pinned_outs():
+        o = [torch.empty((vio.num_cells(w, h, wl["cell"]), 4), dtype=torch.int32).pin_memory().numpy()
+             for w, h in dims]
+        return o, torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+
+    e2e_det = vio.Detector(device=dev.index, max_frames=max(64, n))
+    e2e_det.set_variant(det.tuning()[2])
+    esteps = max(3, min(args.steps, 50))
+    # bytes of one job step: every rank copies its own frames and records
+    h2d = world * sum(w * h for w, h in dims)
+    d2h = world * (sum(16 * vio.num_cells(w, h, wl["cell"]) for w, h in dims) + 4 * n)
+    # synchronous: one vio_detect_host call per step
+    host_outs, host_counts = pinned_outs()
+    for _ in range(3):
+        e2e_det.detect_host(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], host_outs,
+                            host_counts, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(esteps):
+        e2e_det.detect_host(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], host_outs,
+                            host_counts, stream)
+    dt_sync = max_over_ranks(time.perf_counter() - t0)
+    # pipelined: vio_detect_host_async on two alternating streams, so that a
+    # step's frame copies overlap the previous step's kernels
+    streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    bufs = [pinned_outs(), pinned_outs()]
+    for i in range(4):
+        o, c = bufs[i % 2]
+        e2e_det.detect_host_async(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], o, c,
+                                  stream=streams[i % 2])
+    for st in streams:
+        e2e_det.sync(st)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(esteps):
+        o, c = bufs[i % 2]
+        e2e_det.detect_host_async(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], o, c,
+                                  stream=streams[i % 2])
+    for st in streams:
+        e2e_det.sync(st)
+    dt = max_over_ranks(time.perf_counter() - t0)
+    e2e_det.close()
+    return {"value": round(world * esteps * n / dt, 1), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": esteps,
+            "what": "vio_detect_host_async on two alternating streams: pinned host frames copied in, "
+                    "records written into pinned host memory, counts copied back, all inside the timed region",
+            "sync": {"value": round(world * esteps * n / dt_sync, 1), "unit": "frames/s",
+                     "what": "vio_detect_host, one synchronous call per step"}}
+
+
+def barrier():
+    """torch.distributed barrier when a process group is up (no-op otherwise)."""
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
 
 
 def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cptr, n, mpx, ms_per_step):
@@ -504,58 +576,6 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     plain.close()
     out["plain"] = {"value": round(psteps * n / (pms / 1e3), 1), "unit": "frames/s",
                     "what": "same frames, one vio_detect call (and graph replay) per frame"}
-
-    # end to end through the host-buffer entry points (pinned host frames and
-    # outputs): each step copies its frames in and its records out
-    pinned = [torch.from_numpy(f).pin_memory() for f in frames_np]
-    host_frames = [p.numpy() for p in pinned]
-
-    def pinned_outs():
-        o = [torch.empty((vio.num_cells(w, h, wl["cell"]), 4), dtype=torch.int32).pin_memory().numpy()
-             for w, h in dims]
-        return o, torch.empty(n, dtype=torch.int32).pin_memory().numpy()
-
-    e2e_det = vio.Detector(device=dev.index, max_frames=max(64, n))
-    e2e_det.set_variant(det.tuning()[2])
-    esteps = max(3, min(args.steps, 50))
-    h2d = sum(w * h for w, h in dims)
-    d2h = sum(16 * vio.num_cells(w, h, wl["cell"]) for w, h in dims) + 4 * n
-    # synchronous: one vio_detect_host call per step
-    host_outs, host_counts = pinned_outs()
-    for _ in range(3):
-        e2e_det.detect_host(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], host_outs,
-                            host_counts, stream)
-    t0 = time.perf_counter()
-    for _ in range(esteps):
-        e2e_det.detect_host(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], host_outs,
-                            host_counts, stream)
-    dt_sync = time.perf_counter() - t0
-    # pipelined: vio_detect_host_async on two alternating streams, so that a
-    # step's frame copies overlap the previous step's kernels
-    streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
-    bufs = [pinned_outs(), pinned_outs()]
-    for i in range(4):
-        o, c = bufs[i % 2]
-        e2e_det.detect_host_async(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], o, c,
-                                  stream=streams[i % 2])
-    for st in streams:
-        e2e_det.sync(st)
-    t0 = time.perf_counter()
-    for i in range(esteps):
-        o, c = bufs[i % 2]
-        e2e_det.detect_host_async(host_frames, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], o, c,
-                                  stream=streams[i % 2])
-    for st in streams:
-        e2e_det.sync(st)
-    dt = time.perf_counter() - t0
-    e2e_det.close()
-    out["e2e"] = {"value": round(esteps * n / dt, 1), "unit": "frames/s", "h2d_bytes_per_step": h2d,
-                  "d2h_bytes_per_step": d2h, "steps": esteps,
-                  "what": "vio_detect_host_async on two alternating streams: pinned host frames copied in, "
-                          "records written into pinned host memory, counts copied back, all inside the timed "
-                          "region",
-                  "sync": {"value": round(esteps * n / dt_sync, 1), "unit": "frames/s",
-                           "what": "vio_detect_host, one synchronous call per step"}}
 
     if args.serve_seconds > 0:
         out["serving"] = serving_leg(args, dev.index)
