@@ -372,6 +372,8 @@ def run_ours(args, rank, world, local_rank):
         res["detections_per_s"] = round(world * n * npar * args.steps / (ms / 1e3), 1)
     if not args.no_extras and not sweep:
         res["e2e"] = e2e_leg(args, wl, det, dev, stream, frames_np, dims, n, world)
+    if world > 1:
+        args.no_cpu_baseline = True  # the oracle baseline is an N = 1 figure
     if rank == 0 and not args.no_extras:
         res.update(extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cptr, n, mpx,
                           ms_per_step))
