@@ -205,6 +205,34 @@ def test_maximum_frame_size_sampled(dets):
         dets[0].detect([too_big], 15, 9, 64, 3)
 
 
+def test_large4k_sweep_full_launch_sampled(dets):
+    """The 4K sweep exactly as the benchmark launches it: all 32 frames of
+    3840x2160 (seeds 100..131, 400 shapes), 4 levels, 64x64 cells, the 8
+    (thresh, arc) settings in one fused sweep.  Every frame and setting is
+    checked on two blocks of 3x3 cells against the oracle on crops, and the
+    counts against the records."""
+    imgs = [synth.make_frame(3840, 2160, seed=100 + i, n_shapes=400) for i in range(32)]
+    frames = [to_gpu(im) for im in imgs]
+    outs, counts = dets[0].detect_sweep(frames, SWEEP, 64, 4)
+    dets[0].sync()
+    cnt = counts.cpu().numpy()
+    gw, gh = 60, 34
+    rng = np.random.default_rng(11)
+    for i, im in enumerate(imgs):
+        blocks = [(int(rng.integers(0, gw - 3)), int(rng.integers(0, gh - 3))) for _ in range(2)]
+        for p, (thresh, arc) in enumerate(SWEEP):
+            got = outs[p][i].cpu().numpy()
+            assert cnt[p][i] == int((got[:, 2] >= 0).sum())
+            for bx, by in blocks:
+                ox, oy = bx * 64, by * 64
+                cw, ch = min(192, 3840 - ox), min(192, 2160 - oy)
+                want = cells_from_oracle_crop(im, ox, oy, cw, ch, thresh, arc, 64, 4)
+                ncx = (cw + 63) // 64
+                for j in range((ch + 63) // 64):
+                    for k in range(ncx):
+                        assert np.array_equal(got[(by + j) * gw + bx + k], want[j * ncx + k]), (i, p, bx + k, by + j)
+
+
 # ---- edge cases -------------------------------------------------------------
 
 EDGE_SIZES = [(7, 7, 1), (8, 7, 1), (13, 9, 1), (31, 17, 1), (100, 37, 2), (257, 131, 3),
