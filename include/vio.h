@@ -414,6 +414,20 @@ vio_status vio_track(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* co
                      int n_pairs, const float* const* pts, const int* n_pts, const vio_track_params* params,
                      vio_track_result* const* out, vio_stream stream);
 
+/*
+ * vio_track on the detector's output: the features are the records of a
+ * vio_detect / vio_detect_host call on prev[i] (DEVICE arrays of n_cells[i]
+ * vio_feature, one per grid cell), tracked from their (x, y).  out[i]
+ * receives one record per cell; an empty cell (level < 0) gives
+ * {x = -1, y = -1, gain 0, offset 0, status 0, iters 0, residual 0}.  This is
+ * the frontend loop of the paper (detect on one frame, track into the next)
+ * without any copy of the features in between.  Arguments and errors as
+ * vio_track.
+ */
+vio_status vio_track_cells(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* const* next,
+                           const vio_dims* dims, int n_pairs, const vio_feature* const* cells, const int* n_cells,
+                           const vio_track_params* params, vio_track_result* const* out, vio_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,10 +79,12 @@ void vio_track_params_default(vio_track_params* p) {
     p->model = VIO_TRACK_GAIN | VIO_TRACK_OFFSET;
 }
 
-vio_status vio_track(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* const* next, const vio_dims* dims,
-                     int n_pairs, const float* const* pts, const int* n_pts, const vio_track_params* params,
-                     vio_track_result* const* out, vio_stream stream) {
-    NvtxRange nvtx("vio_track");
+namespace {
+
+vio_status track_impl(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* const* next, const vio_dims* dims,
+                      int n_pairs, const void* const* pts_in, const int* n_pts, const vio_track_params* params,
+                      vio_track_result* const* out, vio_stream stream, bool cells_in) {
+    const float* const* pts = reinterpret_cast<const float* const*>(pts_in);
     if (!ctx) return VIO_ERR_INVALID_ARG;
     vio_track_params p;
     if (params) p = *params; else vio_track_params_default(&p);
@@ -204,6 +206,7 @@ vio_status vio_track(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* co
     th->n_features = (int)total;
     th->off_pairs = (uint32_t)off_pairs;
     th->off_prefix = (uint32_t)off_prefix;
+    th->cells_in = cells_in ? 1 : 0;
     prefix[0] = 0;
     for (int i = 0; i < n_pairs; ++i) {
         tps[i].pts = pts[i];
@@ -221,6 +224,24 @@ vio_status vio_track(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* co
     VIO_CK(cudaEventRecord(T.done_ev, s));
     T.have_done = true;
     return VIO_OK;
+}
+
+}  // namespace
+
+vio_status vio_track(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* const* next, const vio_dims* dims,
+                     int n_pairs, const float* const* pts, const int* n_pts, const vio_track_params* params,
+                     vio_track_result* const* out, vio_stream stream) {
+    NvtxRange nvtx("vio_track");
+    return track_impl(ctx, prev, next, dims, n_pairs, reinterpret_cast<const void* const*>(pts), n_pts, params, out,
+                      stream, false);
+}
+
+vio_status vio_track_cells(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* const* next,
+                           const vio_dims* dims, int n_pairs, const vio_feature* const* cells, const int* n_cells,
+                           const vio_track_params* params, vio_track_result* const* out, vio_stream stream) {
+    NvtxRange nvtx("vio_track_cells");
+    return track_impl(ctx, prev, next, dims, n_pairs, reinterpret_cast<const void* const*>(cells), n_cells, params,
+                      out, stream, true);
 }
 
 }  // extern "C"

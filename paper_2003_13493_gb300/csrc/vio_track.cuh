@@ -18,11 +18,12 @@ struct TrackHeader {
     float min_update;
     int32_t model, n_pairs, n_features;
     uint32_t off_pairs, off_prefix;
-    int32_t pad[2];
+    int32_t cells_in;      // 1: the inputs are detector records (x, y, level, score)
+    int32_t pad;
 };
 
 struct TrackPair {
-    const float* pts;   // 2 floats per feature
+    const float* pts;   // 2 floats per feature, or 4 int32 per detector record (cells_in)
     float* out;         // 8 words per feature (vio_track_result)
 };
 
@@ -227,7 +228,24 @@ __global__ void __launch_bounds__(kTrackWarps * 32, 3) track_kernel(const uint8_
     const TrackPair tp = pairs[pr];
     const FrameDesc& fp = cv.fds[2 * pr];
     const FrameDesc& fn = cv.fds[2 * pr + 1];
-    const float x = tp.pts[2 * j], y = tp.pts[2 * j + 1];
+    float x, y;
+    if (th->cells_in) {
+        // a detector record: an empty cell (level < 0) gives an empty result
+        const int4 rec = reinterpret_cast<const int4*>(tp.pts)[j];
+        if (rec.z < 0) {
+            if (lane == 0) {
+                float4* o = reinterpret_cast<float4*>(tp.out + 8 * j);
+                o[0] = make_float4(-1.f, -1.f, 0.f, 0.f);
+                o[1] = make_float4(__int_as_float(0), __int_as_float(0), 0.f, 0.f);
+            }
+            return;
+        }
+        x = (float)rec.x;
+        y = (float)rec.y;
+    } else {
+        x = tp.pts[2 * j];
+        y = tp.pts[2 * j + 1];
+    }
     float tx = 0.f, ty = 0.f, alpha = 0.f, beta = 0.f, residual = 0.f;
     int iters = 0;
     bool ok = true;

@@ -141,6 +141,8 @@ def load(build_if_missing: bool = True):
     lib.vio_track.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(Dims), ci, ctypes.POINTER(P),
                               ctypes.POINTER(ci), ctypes.POINTER(TrackParams), ctypes.POINTER(P), P]
     lib.vio_track.restype = st
+    lib.vio_track_cells.argtypes = lib.vio_track.argtypes
+    lib.vio_track_cells.restype = st
     lib.vio_serve_config_default.argtypes = [ctypes.POINTER(ServeConfig)]
     lib.vio_serve_config_default.restype = None
     lib.vio_serve_start.argtypes = [P, ctypes.POINTER(ServeConfig)]
@@ -306,6 +308,45 @@ class Detector:
         self._check(self.lib.vio_track(self.ctx, pp, nn, dims, n, qp, cnt, ctypes.byref(tp), op,
                                        _stream_handle(stream)))
         return outs
+
+    def track_cells(self, prev, nxt, cells, params: dict | None = None, outs=None, stream=None):
+        """Tracks the detector's records: cells[i] is the (ncells, 4) int32
+        CUDA tensor a detection of prev[i] returned; one (ncells, 8) result
+        per cell (empty cells give status 0)."""
+        import torch
+
+        n = len(prev)
+        if len(nxt) != n or len(cells) != n:
+            raise ValueError("prev, nxt and cells must have one entry per pair")
+        dims = (Dims * n)()
+        pp = (ctypes.c_void_p * n)()
+        nn = (ctypes.c_void_p * n)()
+        for i, (a, b) in enumerate(zip(prev, nxt)):
+            if a.shape != b.shape or a.stride(0) != b.stride(0) or a.dtype != torch.uint8 or not a.is_cuda:
+                raise ValueError("both frames of a pair need the same size and pitch (uint8 CUDA tensors)")
+            dims[i] = Dims(a.shape[1], a.shape[0], a.stride(0))
+            pp[i] = a.data_ptr()
+            nn[i] = b.data_ptr()
+        for c in cells:
+            if c.dtype != torch.int32 or c.dim() != 2 or c.shape[1] != 4 or not c.is_contiguous():
+                raise ValueError("cells must be contiguous (n, 4) int32 tensors")
+        if outs is None:
+            outs = [torch.empty((c.shape[0], TRACK_RESULT_WORDS), dtype=torch.float32, device=c.device) for c in cells]
+        tp = TrackParams()
+        self.lib.vio_track_params_default(ctypes.byref(tp))
+        for k, v in (params or {}).items():
+            setattr(tp, k, v)
+        cp = (ctypes.c_void_p * n)(*[c.data_ptr() for c in cells])
+        cnt = (ctypes.c_int * n)(*[c.shape[0] for c in cells])
+        op = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        self._check(self.lib.vio_track_cells(self.ctx, pp, nn, dims, n, cp, cnt, ctypes.byref(tp), op,
+                                             _stream_handle(stream)))
+        return outs
+
+    def track_cells_ptrs(self, pp, nn, dims, n, cp, cnt, tp, op, stream_handle):
+        """Pre-marshalled vio_track_cells call (ctypes arrays), for timing loops."""
+        self._check(self.lib.vio_track_cells(self.ctx, pp, nn, dims, n, cp, cnt, ctypes.byref(tp), op,
+                                             stream_handle))
 
     def detect_sweep(self, frames, params, cell: int, levels: int, stream=None):
         """params: list of (thresh, arc_len).  Returns (outs[p][i] tensors, counts (n_params, n))."""

@@ -202,3 +202,31 @@ def test_invalid_arguments(det):
                 dict(levels=5)):  # 64 >> 4 = 4 < 7: the smallest level is too small
         with pytest.raises(vio.VioError):
             det.track([img], [img], [q], bad)
+
+
+def test_track_cells_from_the_detector(det):
+    """The frontend loop without a copy of the features: the records of a
+    detection of the previous frame are tracked as they are; every non-empty
+    cell's track equals the oracle's from that cell's position, every empty
+    cell gives an empty result."""
+    prev = synth.smooth_frame(752, 480, seed=21)
+    nxt = synth.smooth_frame(752, 480, seed=21, dx=-1.75, dy=2.5, gain=1.05, offset=-4.0)
+    # a flat 5 x 5-cell block: the cells well inside it hold no corner on any level
+    prev[160:320, 320:480] = 128
+    nxt[160:320, 320:480] = 128
+    gp, gn = torch.from_numpy(prev).cuda(), torch.from_numpy(nxt).cuda()
+    outs, _ = det.detect([gp], 5, 9, 32, 3)
+    params = dict(levels=3, max_iters=12, min_update=0.0, model=3)
+    res = det.track_cells([gp], [gn], outs, params)[0]
+    det.sync()
+    cells = outs[0].cpu().numpy()
+    got = res.cpu().numpy()
+    xy, gain, off, status, iters, resid = vio.track_fields(got)
+    empty = cells[:, 2] < 0
+    assert empty.any() and (~empty).sum() > 50
+    assert (status[empty] == 0).all() and (iters[empty] == 0).all() and (xy[empty] == -1).all()
+    pts = cells[~empty][:, :2].astype(np.float64)
+    L, kw = oracle_params(params)
+    want, mask = converged(prev, nxt, pts, L, kw)
+    assert mask.mean() >= 0.9
+    assert_close(got[~empty], want, mask, exact_iters=True)
