@@ -411,6 +411,40 @@ __device__ __forceinline__ uint32_t coarse4(uint32_t C, uint32_t L, uint32_t R, 
     return keep & 0x80808080u;
 }
 
+// Byte-wise d > t of coarse4, for one word of differences.
+template <bool HIGH_T>
+__device__ __forceinline__ uint32_t byte_gt(uint32_t d, uint32_t k7) {
+    const uint32_t f = (d & 0x7F7F7F7Fu) + k7;
+    return HIGH_T ? (f & d) : (f | d);
+}
+
+// A stronger coarse test on the eight even circle points (0, 2, .., 14: the
+// compass points and the diagonals (+-2, +-2)).  An arc of n >= 9 contiguous
+// points holds at least floor(n/2) >= 4 cyclically consecutive even points,
+// all with |I_x - I_c| > t, so a pixel is kept when four consecutive of the
+// eight differ from the centre by more than t; it never drops a corner.  On
+// the coarser pyramid levels, where a third to a half of the pixels pass
+// coarse4, it halves the pixels that reach the full test.
+//   C, L, R, N, S as in coarse4; UL, UC, UR and DL, DC, DR: the words of C's
+//   column and its neighbours 2 rows up and down.
+template <bool HIGH_T>
+__device__ __forceinline__ uint32_t coarse8(uint32_t C, uint32_t L, uint32_t R, uint32_t N, uint32_t S,
+                                            uint32_t UL, uint32_t UC, uint32_t UR, uint32_t DL, uint32_t DC,
+                                            uint32_t DR, uint32_t k7) {
+    const uint32_t E = __byte_perm(C, R, 0x6543), W = __byte_perm(L, C, 0x4321);
+    // pixels x+2 .. x+5 and x-2 .. x+1 of the rows 2 up and 2 down
+    const uint32_t NE = __byte_perm(UC, UR, 0x5432), NW = __byte_perm(UL, UC, 0x5432);
+    const uint32_t SE = __byte_perm(DC, DR, 0x5432), SW = __byte_perm(DL, DC, 0x5432);
+    const uint32_t fn = byte_gt<HIGH_T>(__vabsdiffu4(N, C), k7), fs = byte_gt<HIGH_T>(__vabsdiffu4(S, C), k7);
+    const uint32_t fe = byte_gt<HIGH_T>(__vabsdiffu4(E, C), k7), fw = byte_gt<HIGH_T>(__vabsdiffu4(W, C), k7);
+    const uint32_t fne = byte_gt<HIGH_T>(__vabsdiffu4(NE, C), k7), fnw = byte_gt<HIGH_T>(__vabsdiffu4(NW, C), k7);
+    const uint32_t fse = byte_gt<HIGH_T>(__vabsdiffu4(SE, C), k7), fsw = byte_gt<HIGH_T>(__vabsdiffu4(SW, C), k7);
+    // the 8 runs of four on the cycle N NE E SE S SW W NW, grouped by their
+    // middle three around a diagonal: run (N..SE) = xne & SE, (NW..E) = NW & xne, ...
+    const uint32_t xne = fn & fne & fe, xse = fe & fse & fs, xsw = fs & fsw & fw, xnw = fw & fnw & fn;
+    return (((xne | xsw) & (fse | fnw)) | ((xse | xnw) & (fne | fsw))) & 0x80808080u;
+}
+
 // ---------------------------------------------------------------------------
 // Fused detect: persistent CTAs pull (frame, level, tile) items from a
 // counter.  A tile is 120 x TH level pixels; its "score region" adds a ring
@@ -497,8 +531,9 @@ __device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x002
 // pair, 16-31 the odd one, 8 pixels per lane).  The kept-pixel bits of up to 4
 // row pairs gather in one 32-bit word per lane (bit 8i + j = pair i, pixel j),
 // one warp scan of the popcounts places each lane's run in the queue, and
-// each lane writes its pixels by walking its set bits.
-template <bool HIGH_T, bool THREE, int TH, int R>
+// each lane writes its pixels by walking its set bits.  EIGHT selects
+// coarse8 (which also reads the rows 2 up and down, inside the 3-row halo).
+template <bool HIGH_T, bool THREE, int TH, int R, bool EIGHT = false>
 __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* queue, int xw, uint32_t k7,
                                                   int warp, int lane, int row_lo, int row_hi, uint32_t vm0,
                                                   uint32_t vm1, uint32_t* status = nullptr) {
@@ -517,8 +552,18 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
         if (r >= row_lo && r < row_hi) {
             const uint32_t* w = reinterpret_cast<const uint32_t*>(img + (3 + r) * G::BW) + xw + 2 * g;
             const uint32_t L = w[-1], C0 = w[0], C1 = w[1], Rt = w[2];
-            const uint32_t k0 = coarse4<HIGH_T, THREE>(C0, L, C1, w[-3 * RW], w[3 * RW], k7) & vm0;
-            const uint32_t k1 = coarse4<HIGH_T, THREE>(C1, C0, Rt, w[1 - 3 * RW], w[1 + 3 * RW], k7) & vm1;
+            uint32_t k0, k1;
+            if (EIGHT) {
+                const uint32_t* u = w - 2 * RW;
+                const uint32_t* d = w + 2 * RW;
+                const uint32_t u0 = u[-1], u1 = u[0], u2 = u[1], u3 = u[2];
+                const uint32_t d0 = d[-1], d1 = d[0], d2 = d[1], d3 = d[2];
+                k0 = coarse8<HIGH_T>(C0, L, C1, w[-3 * RW], w[3 * RW], u0, u1, u2, d0, d1, d2, k7) & vm0;
+                k1 = coarse8<HIGH_T>(C1, C0, Rt, w[1 - 3 * RW], w[1 + 3 * RW], u1, u2, u3, d1, d2, d3, k7) & vm1;
+            } else {
+                k0 = coarse4<HIGH_T, THREE>(C0, L, C1, w[-3 * RW], w[3 * RW], k7) & vm0;
+                k1 = coarse4<HIGH_T, THREE>(C1, C0, Rt, w[1 - 3 * RW], w[1 + 3 * RW], k7) & vm1;
+            }
             m[i >> 2] |= (nibble(k0) | (nibble(k1) << 4)) << (8 * (i & 3));
         }
     }
@@ -676,7 +721,10 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             }
             (void)lx;
             const int xw = xoff / 4;
-            if (high_t) {
+            if (!three && k > 0) {  // levels >= 1: the 8-point test (n <= 11; n >= 12 keeps 3 of 4)
+                total = high_t ? coarse_and_compact<true, false, TH, R, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status)
+                               : coarse_and_compact<false, false, TH, R, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status);
+            } else if (high_t) {
                 total = three ? coarse_and_compact<true, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status)
                               : coarse_and_compact<true, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status);
             } else {

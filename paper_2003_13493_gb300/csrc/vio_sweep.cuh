@@ -134,10 +134,17 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
                 vm1 |= (sx + 4 + j >= xlo && sx + 4 + j < xhi) ? 0x80u << (8 * j) : 0u;
             }
             const int xw = xoff / 4;
-            total = high_t ? coarse_and_compact<true, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo, row_hi,
-                                                                     vm0, vm1, status)
-                           : coarse_and_compact<false, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo, row_hi,
-                                                                      vm0, vm1, status);
+            // levels >= 1: the 8-point test, also a necessary condition for every arc length
+            if (k > 0)
+                total = high_t ? coarse_and_compact<true, false, TH, 1, true>(img, queue, xw, k7, warp, lane, row_lo,
+                                                                              row_hi, vm0, vm1, status)
+                               : coarse_and_compact<false, false, TH, 1, true>(img, queue, xw, k7, warp, lane, row_lo,
+                                                                               row_hi, vm0, vm1, status);
+            else
+                total = high_t ? coarse_and_compact<true, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo,
+                                                                         row_hi, vm0, vm1, status)
+                               : coarse_and_compact<false, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo,
+                                                                          row_hi, vm0, vm1, status);
         }
         __syncwarp();
 

@@ -52,6 +52,67 @@ def test_coarse_test_never_drops_a_corner():
             assert keep, (hex(m), n)
 
 
+def _byte_perm(a, b, sel):
+    """__byte_perm(a, b, sel): result byte i is byte (sel >> 4i) & 7 of b:a."""
+    src = a | (b << 32)
+    return sum(((src >> (8 * ((sel >> (4 * i)) & 7))) & 0xFF) << (8 * i) for i in range(4))
+
+
+def test_coarse_shifts_select_the_circle_columns():
+    """The byte selections of coarse4/coarse8: with C = pixels x..x+3 and
+    its neighbour words L, R, 0x6543 gives x+3.., 0x4321 gives x-3.., 0x5432
+    gives x+2.. from (C, R) and x-2.. from (L, C)."""
+    row = list(range(12))  # pixel values = their column; C holds columns 4..7
+    word = lambda i: sum(row[i + j] << (8 * j) for j in range(4))
+    L, C, R = word(0), word(4), word(8)
+    cols = lambda w: [(w >> (8 * j)) & 0xFF for j in range(4)]
+    assert cols(_byte_perm(C, R, 0x6543)) == [7, 8, 9, 10]
+    assert cols(_byte_perm(L, C, 0x4321)) == [1, 2, 3, 4]
+    assert cols(_byte_perm(C, R, 0x5432)) == [6, 7, 8, 9]
+    assert cols(_byte_perm(L, C, 0x5432)) == [2, 3, 4, 5]
+
+
+def _eight(f):
+    """coarse8's keep formula on the flags of N, NE, E, SE, S, SW, W, NW."""
+    fn, fne, fe, fse, fs, fsw, fw, fnw = f
+    xne, xse, xsw, xnw = fn & fne & fe, fe & fse & fs, fs & fsw & fw, fw & fnw & fn
+    return ((xne | xsw) & (fse | fnw)) | ((xse | xnw) & (fne | fsw))
+
+
+def test_eight_point_formula_is_four_consecutive():
+    """The grouped formula equals 'four cyclically consecutive of the eight'
+    for all 256 flag patterns, and implies the compass two-adjacent rule."""
+    for m in range(256):
+        f = [(m >> i) & 1 for i in range(8)]
+        runs = any(all(f[(s + j) % 8] for j in range(4)) for s in range(8))
+        assert bool(_eight(f)) == runs, m
+        if runs:
+            assert (f[0] | f[4]) & (f[2] | f[6])
+
+
+def test_eight_point_test_never_drops_a_corner():
+    """Every 16-point mask with a cyclic run of n (9..16) has four
+    consecutive even points (0, 2, .., 14) set, so coarse8 keeps it."""
+    for n in range(9, 17):
+        for m in range(1 << 16):
+            if _has_run(m, n):
+                assert _eight([(m >> (2 * i)) & 1 for i in range(8)]), (hex(m), n)
+
+
+def test_even_circle_points_are_compass_and_diagonals():
+    """The Bresenham circle of radius 3 (points numbered clockwise from the
+    top, as in FAST) has its even points at the compass points and the four
+    (+-2, +-2) diagonals, in the cyclic order coarse8 assumes."""
+    circle = [(0, -3), (1, -3), (2, -2), (3, -1), (3, 0), (3, 1), (2, 2), (1, 3),
+              (0, 3), (-1, 3), (-2, 2), (-3, 1), (-3, 0), (-3, -1), (-2, -2), (-1, -3)]
+    ring = {(x, y) for x in range(-3, 4) for y in range(-3, 4) if 2.5 <= (x * x + y * y) ** 0.5 < 3.5}
+    assert set(circle) == ring and len(circle) == 16
+    # clockwise from the top in image coordinates (y down)
+    ang = [np.arctan2(x, -y) % (2 * np.pi) for x, y in circle]
+    assert ang == sorted(ang)
+    assert circle[0::2] == [(0, -3), (2, -2), (3, 0), (2, 2), (0, 3), (-2, 2), (-3, 0), (-2, -2)]
+
+
 def test_arc_starts_doubling():
     """arc_starts: runs of n from three AND-shift doublings plus an overlap."""
     for n in range(9, 17):
