@@ -593,6 +593,31 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
     return __shfl_sync(0xFFFFFFFFu, incl, 31);
 }
 
+// Start of a tile's score writes.  The score tile is reused from tile to
+// tile without a barrier after the NMS: each consumer warp arrives on
+// nms_bar when its NMS of tile t-1 is done, and before writing the scores of
+// tile t (its own rows only) waits for that phase and zeroes its own rows, so
+// no warp's NMS can still be reading them.  Returns false on a timed-out
+// wait (status set).  T: the tile's element type (rows of G::SW elements).
+template <int TH, int R, typename T>
+__device__ __forceinline__ bool own_rows_reset(uint64_t* nms_bar, int t, T* tile, int warp, int lane,
+                                               uint32_t* status) {
+    using G = TileGeom<TH, R>;
+    static_assert(2 * G::PPW * G::WARPS == G::SR, "warps own all score rows");
+    constexpr int N16 = 2 * G::PPW * G::SW * (int)sizeof(T) / 16;  // 16-byte words per warp
+    static_assert(N16 % 32 == 0, "whole 16-byte stores per lane");
+    if (t == 0) return true;  // zeroed at kernel start
+    if (!mbar_wait_bounded(nms_bar, (t - 1) & 1, kWaitLimitNs)) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        return false;
+    }
+    uint4* own = reinterpret_cast<uint4*>(tile + 2 * G::PPW * warp * G::SW);
+#pragma unroll
+    for (int j = 0; j < N16 / 32; ++j) own[lane + 32 * j] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    return true;
+}
+
 // Producer of the detect kernels (one thread): claims work items from the
 // counter one ahead of their use, decodes each into the tile it covers and
 // issues the TMA load of the tile and its halo into the next buffer of the
@@ -645,7 +670,7 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
     using G = TileGeom<TH, R>;
     constexpr int NB = G::NBUF;
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    __shared__ uint64_t full_bar[NB], empty_bar[NB];
+    __shared__ uint64_t full_bar[NB], empty_bar[NB], nms_bar;
     __shared__ ItemInfo info[NB];
     // the tile table, copied once so that the producer's search stays on chip
     constexpr int kTileCache = 512;
@@ -663,9 +688,11 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             mbar_init(&full_bar[b], 1);
             mbar_init(&empty_bar[b], kConsumers / 32);  // one arrival per consumer warp
         }
+        mbar_init(&nms_bar, kConsumers / 32);
         fence_barrier_init();
     }
-    // the score tile starts zero; only corners are written, and reset after use
+    // the score tile starts zero; only corners are written, and each warp
+    // zeroes its rows before the next tile's writes
     for (int i = tid; i < G::SR * G::SW / 8; i += kThreads) reinterpret_cast<uint4*>(sc)[i] = make_uint4(0, 0, 0, 0);
     // the decode kernel adds up the per-frame counts from zero
     if (blockIdx.x == 0 && cv.h->counts)
@@ -752,6 +779,7 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             if (s) queue[ncorner + __popc(cm & lt_mask)] = (uint16_t)idx;
             ncorner += __popc(cm);
         }
+        if (!own_rows_reset<TH, R>(&nms_bar, t, sc, warp, lane, status)) return;
         for (int e = lane; e < ncorner; e += 32) {
             const int idx = queue[e];
             const uint8_t* p = img_base + idx + 16 * (idx >> 7);
@@ -811,11 +839,9 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
                 }
             }
         }
-        named_barrier(1, kConsumers);  // every warp's NMS has read its neighbours
-        for (int e = lane; e < ncorner; e += 32) sc[queue[e]] = 0;
-        // the next tile's scores are written only after its coarse pass and a
-        // __syncwarp; the reset of another warp's rows is ordered by the
-        // named barrier that follows the next tile's full test
+        // this warp's NMS reads of the score tile are done
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&nms_bar);
     }
 }
 

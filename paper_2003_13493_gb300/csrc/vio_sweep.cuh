@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
     using G = SweepGeom<TH>;
     constexpr int NB = G::NBUF;
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    __shared__ uint64_t full_bar[NB], empty_bar[NB];
+    __shared__ uint64_t full_bar[NB], empty_bar[NB], nms_bar;
     __shared__ ItemInfo info[NB];
     constexpr int kTileCache = 512;
     __shared__ int32_t tiles_sh[kTileCache];
@@ -73,13 +73,15 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             mbar_init(&full_bar[b], 1);
             mbar_init(&empty_bar[b], kConsumers / 32);
         }
+        mbar_init(&nms_bar, kConsumers / 32);
         fence_barrier_init();
     }
     if (tid < kMaxSweep) {
         set_t[tid] = tid < n_set ? sw->thresh[tid] : 0;
         set_n[tid] = tid < n_set ? sw->arc[tid] : 16;
     }
-    // score and setting-mask tiles start zero; only corners are written, and reset after use
+    // score and setting-mask tiles start zero; only corners are written, and
+    // each warp zeroes its rows before the next tile's writes
     for (int i = tid; i < G::SR * G::SW / 8; i += kThreads) reinterpret_cast<uint4*>(sc)[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < G::SR * G::SW / 16; i += kThreads) reinterpret_cast<uint4*>(mk)[i] = make_uint4(0, 0, 0, 0);
     if (blockIdx.x == 0)
@@ -148,6 +150,11 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
         }
         __syncwarp();
 
+        // the score and mask rows of this warp are free once every warp's NMS
+        // of the previous tile is done
+        if (!own_rows_reset<TH, 1>(&nms_bar, t, sc, warp, lane, status) ||
+            !own_rows_reset<TH, 1>(&nms_bar, t, mk, warp, lane, status))
+            return;
         // full test of every setting; corners (in any setting) compacted in place
         int ncorner = 0;
         const uint8_t* img_base = img + 3 * G::BW + xoff;
@@ -244,12 +251,9 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
                 }
             }
         }
-        named_barrier(1, kConsumers);  // every warp's NMS has read its neighbours
-        for (int e = lane; e < ncorner; e += 32) {
-            const int idx = queue[e];
-            sc[idx] = 0;
-            mk[idx] = 0;
-        }
+        // this warp's NMS reads of the score and mask tiles are done
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&nms_bar);
     }
 }
 
