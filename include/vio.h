@@ -174,12 +174,18 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
 /*
  * Same as vio_detect for frames and results in HOST memory; the call returns
  * when host_cells (host, per frame) and host_counts (host int32[n_frames] or
- * NULL) are written.  Frames in pinned (page-locked) memory whose address and
- * pitch are multiples of 16 are read by the pyramid kernel through their
- * device mapping, which also writes the device copy of level 0 (one pass over
- * the host link, overlapped with the pyramid); other frames are copied by the
- * copy engines.  Records for pinned, 16-byte aligned host_cells are written
- * in place by the decode kernel; others come back through a staging copy.
+ * NULL) are written.  Upload: frames that lie one after another in host
+ * memory (address and pitch multiples of 16, rows padded by at most 256
+ * bytes, at most 4096 bytes between a frame's last pixel and the next
+ * frame) are copied as one span by one copy-engine copy (a copy costs about
+ * 2 us on top of its bytes, so 64 frames in one buffer upload about 1.5x
+ * faster than 64 separate ones); a frame alone in pinned (page-locked)
+ * memory with address and pitch multiples of 16 is read by the pyramid
+ * kernel through its device mapping, which also writes the device copy of
+ * level 0 (one pass over the host link, overlapped with the pyramid); other
+ * frames are copied one by one.  Records for pinned, 16-byte aligned
+ * host_cells are written in place by the decode kernel; others come back
+ * through a staging copy.
  */
 vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims,
                            int n_frames, int thresh, int arc_len, int cell_size, int levels,
@@ -188,7 +194,9 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
 /*
  * Asynchronous form of vio_detect_host for pipelining batches: it enqueues
  * the copy of the frames into one of three rotating device input slots (copy
- * engines), the detection and the result writes on `stream` and returns.
+ * engines; frames that lie one after another in host memory as one span, as
+ * in vio_detect_host), the detection and the result writes on `stream` and
+ * returns.
  * The results are valid after vio_sync(ctx, stream).  Calls on different
  * streams overlap their frame copies with the previous call's kernels (the
  * kernels of one context still run one call after another).

@@ -369,6 +369,67 @@ def test_host_path_pinned_buffers(dets, mixed):
     assert_parity(got, counts, imgs, 15, 9, 32, 1, 0)
 
 
+def arena_frames(imgs, layout, pinned=True):
+    """Frames placed in one host buffer: layout[i] = (gap bytes before frame
+    i, row pitch or 0 for w).  Returns the buffer and numpy views."""
+    spans = []
+    off = 0
+    for im, (gap, pitch) in zip(imgs, layout):
+        h, w = im.shape
+        pitch = pitch or w
+        off += gap
+        spans.append((off, pitch))
+        off += pitch * (h - 1) + w
+    buf = torch.zeros(off + 64, dtype=torch.uint8)
+    if pinned:
+        buf = buf.pin_memory()
+    a = buf.numpy()
+    views = []
+    for im, (o, pitch) in zip(imgs, spans):
+        h, w = im.shape
+        v = np.lib.stride_tricks.as_strided(a[o:], shape=(h, w), strides=(pitch, 1))
+        v[...] = im
+        views.append(v)
+    return buf, views
+
+
+def test_host_frames_in_one_buffer(dets, mixed):
+    """Frames that lie one after another in host memory are uploaded as
+    spans (one copy each); gaps, padded rows, a misaligned frame, a large gap
+    and a frame below its predecessor split the spans.  Every layout, pinned
+    or pageable, synchronous or pipelined, must give the oracle's records."""
+    imgs = [mixed[i] for i in (0, 17, 33, 50, 5, 21, 40, 60)]
+    layouts = {
+        "packed": [(0, 0)] * len(imgs),
+        "gaps and padded rows": [(0, 0), (48, 768), (16, 0), (0, 1936), (4096, 0), (32, 1280), (0, 0), (0, 2048)],
+        "misaligned and far": [(0, 0), (0, 0), (3, 0), (13, 0), (8192, 0), (0, 0), (16, 0), (0, 0)],
+    }
+    for name, layout in layouts.items():
+        for pinned in (True, False):
+            buf, frames = arena_frames(imgs, layout, pinned)
+            got, counts = dets[0].detect_host(frames, 15, 9, 32, 3)
+            assert_parity(got, counts, imgs, 15, 9, 32, 3, 0)
+            if pinned:
+                outs = []
+                keep = []
+                for im in imgs:
+                    b, v = pinned_like(np.zeros((vio.num_cells(im.shape[1], im.shape[0], 32), 4), np.int32))
+                    keep.append(b)
+                    outs.append(v)
+                b, c = pinned_like(np.zeros(len(imgs), np.int32))
+                keep.append(b)
+                dets[0].detect_host_async(frames, 15, 9, 32, 3, outs, c)
+                dets[0].sync()
+                assert_parity(outs, c, imgs, 15, 9, 32, 3, 0)
+    # frames in reverse address order: every frame its own span
+    buf, frames = arena_frames(imgs, layouts["packed"])
+    got, counts = dets[0].detect_host(frames[::-1], 15, 9, 32, 3)
+    assert_parity(got, counts, imgs[::-1], 15, 9, 32, 3, 0)
+    # one level: no pyramid kernel
+    got, counts = dets[0].detect_host(frames, 15, 9, 32, 1)
+    assert_parity(got, counts, imgs, 15, 9, 32, 1, 0)
+
+
 def test_host_async_pipelined_on_two_streams(dets, mixed):
     """Batches alternate between two streams with rotating input slots; every
     batch's records must equal the oracle once its stream is synchronised."""
