@@ -593,24 +593,36 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
     return __shfl_sync(0xFFFFFFFFu, incl, 31);
 }
 
-// Start of a tile's score writes.  The score tile is reused from tile to
-// tile without a barrier after the NMS: each consumer warp arrives on
-// nms_bar when its NMS of tile t-1 is done, and before writing the scores of
-// tile t (its own rows only) waits for that phase and zeroes its own rows, so
-// no warp's NMS can still be reading them.  Returns false on a timed-out
-// wait (status set).  T: the tile's element type (rows of G::SW elements).
+// Consumer warps synchronise with their neighbours only.  Warp w owns score
+// rows [2*PPW*w, 2*PPW*(w+1)) and its NMS reads R <= 2*PPW rows beyond them,
+// so only warps w-1 and w+1 read its rows.  Per tile t each warp arrives on
+// sc_bar[w] once its scores are written and on nms_bar[w] once its NMS is
+// done (one arrival per phase, phase t for tile t).  Before its NMS a warp
+// waits for phase t of its neighbours' sc_bar; before writing the scores of
+// tile t (its own rows only) it waits for phase t-1 of its neighbours'
+// nms_bar and zeroes its rows.  A warp can thus run at most one phase ahead
+// of a neighbour, which keeps the parity waits exact.  Returns false on a
+// timed-out wait (status set).
+__device__ __forceinline__ bool neighbours_wait(uint64_t* bars, int warp, int n_warps, uint32_t parity, int lane,
+                                                uint32_t* status) {
+    const bool ok = (warp == 0 || mbar_wait_bounded(&bars[warp - 1], parity, kWaitLimitNs)) &&
+                    (warp == n_warps - 1 || mbar_wait_bounded(&bars[warp + 1], parity, kWaitLimitNs));
+    if (!ok && lane == 0) atomicOr(status, kStatusTimeout);
+    return ok;
+}
+
+// Start of a tile's score writes (see neighbours_wait).  T: the tile's
+// element type (rows of G::SW elements).
 template <int TH, int R, typename T>
-__device__ __forceinline__ bool own_rows_reset(uint64_t* nms_bar, int t, T* tile, int warp, int lane,
+__device__ __forceinline__ bool own_rows_reset(uint64_t* nms_bars, int t, T* tile, int warp, int lane,
                                                uint32_t* status) {
     using G = TileGeom<TH, R>;
     static_assert(2 * G::PPW * G::WARPS == G::SR, "warps own all score rows");
+    static_assert(R <= 2 * G::PPW, "the NMS reads the rows of adjacent warps only");
     constexpr int N16 = 2 * G::PPW * G::SW * (int)sizeof(T) / 16;  // 16-byte words per warp
     static_assert(N16 % 32 == 0, "whole 16-byte stores per lane");
     if (t == 0) return true;  // zeroed at kernel start
-    if (!mbar_wait_bounded(nms_bar, (t - 1) & 1, kWaitLimitNs)) {
-        if (lane == 0) atomicOr(status, kStatusTimeout);
-        return false;
-    }
+    if (!neighbours_wait(nms_bars, warp, G::WARPS, (t - 1) & 1, lane, status)) return false;
     uint4* own = reinterpret_cast<uint4*>(tile + 2 * G::PPW * warp * G::SW);
 #pragma unroll
     for (int j = 0; j < N16 / 32; ++j) own[lane + 32 * j] = make_uint4(0u, 0u, 0u, 0u);
@@ -670,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
     using G = TileGeom<TH, R>;
     constexpr int NB = G::NBUF;
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    __shared__ uint64_t full_bar[NB], empty_bar[NB], nms_bar;
+    __shared__ uint64_t full_bar[NB], empty_bar[NB], sc_bar[G::WARPS], nms_bar[G::WARPS];
     __shared__ ItemInfo info[NB];
     // the tile table, copied once so that the producer's search stays on chip
     constexpr int kTileCache = 512;
@@ -688,7 +700,10 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             mbar_init(&full_bar[b], 1);
             mbar_init(&empty_bar[b], kConsumers / 32);  // one arrival per consumer warp
         }
-        mbar_init(&nms_bar, kConsumers / 32);
+        for (int w = 0; w < G::WARPS; ++w) {
+            mbar_init(&sc_bar[w], 1);
+            mbar_init(&nms_bar[w], 1);
+        }
         fence_barrier_init();
     }
     // the score tile starts zero; only corners are written, and each warp
@@ -779,16 +794,20 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             if (s) queue[ncorner + __popc(cm & lt_mask)] = (uint16_t)idx;
             ncorner += __popc(cm);
         }
-        if (!own_rows_reset<TH, R>(&nms_bar, t, sc, warp, lane, status)) return;
+        if (!own_rows_reset<TH, R>(nms_bar, t, sc, warp, lane, status)) return;
         for (int e = lane; e < ncorner; e += 32) {
             const int idx = queue[e];
             const uint8_t* p = img_base + idx + 16 * (idx >> 7);
             sc[idx] = (uint16_t)(MODE == 0 ? sad_b<G::BW>(p) : eval_corner<MODE, G::BW, true>(p, thresh, n_arc));
         }
-        // this warp is done with the image buffer
+        // this warp is done with the image buffer, and its scores are written
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty_bar[b]);
-        named_barrier(1, kConsumers);  // all scores of the tile are written
+        if (lane == 0) {
+            mbar_arrive(&empty_bar[b]);
+            mbar_arrive(&sc_bar[warp]);
+        }
+        // the neighbours' scores of this tile are written
+        if (!neighbours_wait(sc_bar, warp, G::WARPS, t & 1, lane, status)) return;
 
         // 4. NMS on the corners, per-cell warp reduction, atomicMax
         for (int e0 = 0; e0 < ncorner; e0 += 32) {
@@ -841,7 +860,7 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
         }
         // this warp's NMS reads of the score tile are done
         __syncwarp();
-        if (lane == 0) mbar_arrive(&nms_bar);
+        if (lane == 0) mbar_arrive(&nms_bar[warp]);
     }
 }
 

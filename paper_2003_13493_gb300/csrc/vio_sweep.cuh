@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
     using G = SweepGeom<TH>;
     constexpr int NB = G::NBUF;
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    __shared__ uint64_t full_bar[NB], empty_bar[NB], nms_bar;
+    __shared__ uint64_t full_bar[NB], empty_bar[NB], sc_bar[G::WARPS], nms_bar[G::WARPS];
     __shared__ ItemInfo info[NB];
     constexpr int kTileCache = 512;
     __shared__ int32_t tiles_sh[kTileCache];
@@ -73,7 +73,10 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             mbar_init(&full_bar[b], 1);
             mbar_init(&empty_bar[b], kConsumers / 32);
         }
-        mbar_init(&nms_bar, kConsumers / 32);
+        for (int w = 0; w < G::WARPS; ++w) {
+            mbar_init(&sc_bar[w], 1);
+            mbar_init(&nms_bar[w], 1);
+        }
         fence_barrier_init();
     }
     if (tid < kMaxSweep) {
@@ -150,10 +153,10 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
         }
         __syncwarp();
 
-        // the score and mask rows of this warp are free once every warp's NMS
-        // of the previous tile is done
-        if (!own_rows_reset<TH, 1>(&nms_bar, t, sc, warp, lane, status) ||
-            !own_rows_reset<TH, 1>(&nms_bar, t, mk, warp, lane, status))
+        // the score and mask rows of this warp are free once its neighbours'
+        // NMS of the previous tile is done
+        if (!own_rows_reset<TH, 1>(nms_bar, t, sc, warp, lane, status) ||
+            !own_rows_reset<TH, 1>(nms_bar, t, mk, warp, lane, status))
             return;
         // full test of every setting; corners (in any setting) compacted in place
         int ncorner = 0;
@@ -192,9 +195,14 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             const int idx = queue[e];
             sc[idx] = (uint16_t)sad_b<G::BW>(img_base + idx + 16 * (idx >> 7));
         }
+        // this warp is done with the image buffer, and its scores and masks are written
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty_bar[b]);
-        named_barrier(1, kConsumers);  // all scores and masks of the tile are written
+        if (lane == 0) {
+            mbar_arrive(&empty_bar[b]);
+            mbar_arrive(&sc_bar[warp]);
+        }
+        // the neighbours' scores and masks of this tile are written
+        if (!neighbours_wait(sc_bar, warp, G::WARPS, t & 1, lane, status)) return;
 
         // 3x3 NMS of every setting at once: a neighbour suppresses the pixel
         // in the settings where it is a corner with a higher score
@@ -253,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
         }
         // this warp's NMS reads of the score and mask tiles are done
         __syncwarp();
-        if (lane == 0) mbar_arrive(&nms_bar);
+        if (lane == 0) mbar_arrive(&nms_bar[warp]);
     }
 }
 
