@@ -207,9 +207,9 @@ def measured_peaks():
 
 # ---- CPU oracle leg ------------------------------------------------------------
 
-def oracle_rate(frames, wl, seconds: float):
+def oracle_rate(frames, wl, seconds: float, cores: int = 0):
     """Frames/s of the plain C oracle over a bounded sample, frame-parallel on
-    the host cores (ctypes releases the GIL)."""
+    `cores` threads (all host cores by default; ctypes releases the GIL)."""
     from concurrent.futures import ThreadPoolExecutor
 
     import oracle
@@ -219,7 +219,7 @@ def oracle_rate(frames, wl, seconds: float):
     for f in frames:
         by_size.setdefault(f.shape, []).append(f)
     sample = [v[i] for v in by_size.values() for i in range(min(2, len(v)))]
-    cores = os.cpu_count() or 1
+    cores = cores or os.cpu_count() or 1
     settings = wl.get("sweep") or [(wl["thresh"], wl["arc"])]
 
     def one(im):  # a frame is done when every setting of the workload is
@@ -600,8 +600,11 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
 
     if not args.no_cpu_baseline:
         rate, cores, sample = oracle_rate(frames_np, wl, args.cpu_seconds)
+        rate1, _, sample1 = oracle_rate(frames_np, wl, args.cpu_seconds / 3, cores=1)
         out["cpu_baseline"] = {"value": round(rate, 2), "unit": "frames/s", "cores": cores, "kind": "oracle",
-                               "sample": sample}
+                               "sample": sample,
+                               "single_core": {"value": round(rate1, 2), "unit": "frames/s", "cores": 1,
+                                               "sample": sample1}}
     return out
 
 
