@@ -514,6 +514,8 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
         # what binds instead: integer issue (ncu on the same kernel source)
         out["roofline"]["alu"] = {"pipe_alu_pct": float(prof_vals["alu_pipe_pct"]),
                                   "issue_active_pct": float(prof_vals["issue_active_pct"]),
+                                  "binds": "integer issue: the ALU pipe is this busy while DRAM moves the "
+                                           "algorithmic bytes at the HBM fraction above",
                                   "source": f"profiles/{kname.replace('_kernel', '')}_{args.workload}.md"}
     out["stage_ms"] = {"pyramid": round(stage[0], 5), kname.replace("_kernel", ""): round(stage[1], 5),
                        "decode": round(stage[2], 5)}
@@ -593,6 +595,7 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     out["plain"] = {"value": round(psteps * n / (pms / 1e3), 1), "unit": "frames/s",
                     "what": "same frames, one vio_detect call (and graph replay) per frame"}
 
+    out["latency"] = latency_leg(args, dev.index)
     if args.serve_seconds > 0:
         out["serving"] = serving_leg(args, dev.index)
     if not args.no_tracker:
@@ -790,6 +793,61 @@ def tracker_leg(args, dev_index: int) -> dict:
         out["cpu_baseline"] = {"value": round(done / (time.perf_counter() - t0), 1), "unit": "features/s",
                                "cores": 1, "kind": "oracle",
                                "sample": f"{done} features of the same pairs, fp64 numpy, one thread"}
+    return out
+
+
+def latency_leg(args, dev_index: int) -> dict:
+    """Per-frame latency of one 752x480 frame per call, synchronised after
+    every call: the single-frame workloads (seed 0: FAST-9, thresh 10, one
+    level; seed 1: thresh 20, 3 levels; 32x32 cells).  'device': frame and
+    cells in device memory (vio_detect, then vio_sync); 'host': pinned host
+    frame in, records into pinned host memory (vio_detect_host, upload and
+    download included)."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2003_13493_gb300 import synth, vio
+
+    dev = torch.device("cuda", dev_index)
+    stream = torch.cuda.current_stream(dev)
+    sh = vio._stream_handle(stream)
+    w, h, reps = 752, 480, 400
+    ncell = vio.num_cells(w, h, 32)
+    out = {}
+    for name, seed, thresh, levels in (("seed0_1level", 0, 10, 1), ("seed1_3levels", 1, 20, 3)):
+        img = synth.make_frame(w, h, seed)
+        det = vio.Detector(device=dev_index, max_frames=1)
+        g = torch.from_numpy(img).to(dev)
+        cells = torch.empty((ncell, 4), dtype=torch.int32, device=dev)
+        hf = torch.from_numpy(img).pin_memory()
+        hc = torch.empty((ncell, 4), dtype=torch.int32).pin_memory()
+        dims = (vio.Dims * 1)(vio.Dims(w, h, w))
+        fd = (ctypes.c_void_p * 1)(g.data_ptr())
+        od = (ctypes.c_void_p * 1)(cells.data_ptr())
+        fh = (ctypes.c_void_p * 1)(hf.data_ptr())
+        oh = (ctypes.c_void_p * 1)(hc.data_ptr())
+        res = {}
+        for kind in ("device", "host"):
+            ts = []
+            for i in range(reps + 20):
+                t0 = time.perf_counter()
+                if kind == "device":
+                    det.detect_ptrs(fd, dims, 1, thresh, 9, 32, levels, od, None, sh)
+                    det.sync(stream)
+                else:
+                    det._check(det.lib.vio_detect_host(det.ctx, fh, dims, 1, thresh, 9, 32, levels, oh, None, sh))
+                if i >= 20:
+                    ts.append((time.perf_counter() - t0) * 1e6)
+            res[kind] = {"p50_us": round(float(np.percentile(ts, 50)), 1),
+                         "p99_us": round(float(np.percentile(ts, 99)), 1)}
+        same = bool(np.array_equal(cells.cpu().numpy(), hc.numpy()))
+        det.close()
+        out[name] = {**res, "same_cells": same}
+    out["what"] = ("one 752x480 frame per call, synchronised after every call (host clock): device-resident "
+                   "(vio_detect + vio_sync) and host buffers (vio_detect_host, pinned frame in, pinned "
+                   "records out); seed 0 at one level (thresh 10), seed 1 at three (thresh 20)")
     return out
 
 
