@@ -206,6 +206,31 @@ def _stream_handle(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(int(h) if h else 0)
 
 
+class HostBatch:
+    """Host frames and result buffers marshalled once for repeated
+    vio_detect_host / vio_detect_host_async calls on the same buffers (a
+    camera ring's fixed slots): frames are 2-D uint8 numpy arrays, outs numpy
+    int32 (n_cells, 4) arrays (pinned for the asynchronous call), counts an
+    int32 array or None.  The caller rewrites the buffers' contents between
+    calls; the arrays must stay alive while the batch is used."""
+
+    def __init__(self, frames, outs, counts=None):
+        n = len(frames)
+        if len(outs) != n:
+            raise ValueError("one output array per frame")
+        self.n = n
+        self.dims = (Dims * n)()
+        self.fptr = (ctypes.c_void_p * n)()
+        for i, f in enumerate(frames):
+            if f.dtype != np.uint8 or f.ndim != 2 or f.strides[1] != 1:
+                raise ValueError("frames must be 2-D uint8 arrays with unit column stride")
+            self.dims[i] = Dims(f.shape[1], f.shape[0], f.strides[0])
+            self.fptr[i] = f.ctypes.data
+        self.optr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+        self.cptr = ctypes.c_void_p(counts.ctypes.data) if counts is not None else None
+        self._keep = (frames, outs, counts)
+
+
 class Detector:
     """One library context on one device."""
 
@@ -401,6 +426,14 @@ class Detector:
                                              ctypes.c_void_p(counts.ctypes.data),
                                              _stream_handle(stream) if stream is not None else ctypes.c_void_p(0)))
         return outs, counts
+
+    def detect_host_batch(self, batch: "HostBatch", thresh: int, arc_len: int, cell: int, levels: int,
+                          stream=None, pipelined: bool = False):
+        """vio_detect_host (or, pipelined, vio_detect_host_async) on a
+        HostBatch: no per-call marshalling."""
+        fn = self.lib.vio_detect_host_async if pipelined else self.lib.vio_detect_host
+        self._check(fn(self.ctx, batch.fptr, batch.dims, batch.n, thresh, arc_len, cell, levels, batch.optr,
+                       batch.cptr, _stream_handle(stream) if stream is not None else ctypes.c_void_p(0)))
 
     def detect_host_async(self, frames, thresh: int, arc_len: int, cell: int, levels: int, outs, counts=None,
                           stream=None):

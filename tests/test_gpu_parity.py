@@ -430,6 +430,31 @@ def test_host_frames_in_one_buffer(dets, mixed):
     assert_parity(got, counts, imgs, 15, 9, 32, 1, 0)
 
 
+def test_host_batch_reuses_marshalled_buffers(dets, mixed):
+    """A HostBatch is marshalled once; each call reads the frames' current
+    contents (rewritten between calls) and writes the records in place."""
+    first = [mixed[i] for i in (1, 18, 35, 52)]
+    second = [mixed[i] for i in (9, 26, 43, 60)]  # same sizes, other content
+    keep = []
+    buf, frames = arena_frames(first, [(0, 0)] * 4)
+    outs = []
+    for im in first:
+        b, v = pinned_like(np.zeros((vio.num_cells(im.shape[1], im.shape[0], 32), 4), np.int32))
+        keep.append(b)
+        outs.append(v)
+    b, counts = pinned_like(np.zeros(4, np.int32))
+    keep.append(b)
+    batch = vio.HostBatch(frames, outs, counts)
+    for imgs in (first, second, first):
+        for f, im in zip(frames, imgs):
+            f[...] = im
+        dets[0].detect_host_batch(batch, 15, 9, 32, 3)
+        assert_parity(outs, counts, imgs, 15, 9, 32, 3, 0)
+        dets[0].detect_host_batch(batch, 15, 9, 32, 3, pipelined=True)
+        dets[0].sync()
+        assert_parity(outs, counts, imgs, 15, 9, 32, 3, 0)
+
+
 def test_host_async_pipelined_on_two_streams(dets, mixed):
     """Batches alternate between two streams with rotating input slots; every
     batch's records must equal the oracle once its stream is synchronised."""
