@@ -33,12 +33,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Barrier over the first `count` threads of the CTA (a multiple of 32),
-// separate from __syncthreads (barrier 0).
-__device__ __forceinline__ void named_barrier(uint32_t id, uint32_t count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
 // One potentially blocking test of the phase: a thread whose phase is not
 // complete is suspended until it completes or the time hint (ns) passes, so
 // a waiting warp takes no issue slots from the warps doing the work.

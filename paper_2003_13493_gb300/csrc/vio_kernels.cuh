@@ -753,7 +753,6 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             const int row_lo = max(0, 3 - y0 + R), row_hi = min(G::SR, Hk - 3 - y0 + R);
             // NMS needs scores of score columns 4-R .. 123+R (x0-R .. x0+119+R) only
             const int sx = 8 * (lane & 15);           // score column of this lane's first pixel
-            const int lx = x0 - 4 + sx;               // its level x
             const int xlo = max(4 - R, 7 - x0), xhi = min(124 + R, Wk + 1 - x0);  // kept score columns [xlo, xhi)
             uint32_t vm0 = 0, vm1 = 0;
 #pragma unroll
@@ -761,7 +760,6 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
                 vm0 |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
                 vm1 |= (sx + 4 + j >= xlo && sx + 4 + j < xhi) ? 0x80u << (8 * j) : 0u;
             }
-            (void)lx;
             const int xw = xoff / 4;
             if (!three && k > 0) {  // levels >= 1: the 8-point test (n <= 11; n >= 12 keeps 3 of 4)
                 total = high_t ? coarse_and_compact<true, false, TH, R, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status)
