@@ -163,9 +163,16 @@ ShapeKey shape_key(const vio_dims* dims, int n, int cell, int levels) {
     return k;
 }
 
+constexpr int kSmallDecodeCtas = 8;  // decode grid of a small call
+
 // Enqueues pyramid -> fused detect -> decode on `s`; launch shapes depend only
-// on the context (the kernels read the batch from the call block).
-vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s, bool pyramid = true) {
+// on the context and on `small` (the kernels read the batch from the call
+// block and stride over whatever grid they get).  A small call (a few frames
+// of VGA size: at most one detect item, two pyramid blocks per SM) launches
+// one CTA per SM instead of filling every SM, which saves the start-up of CTAs
+// that would find no work.
+vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s, bool pyramid = true,
+                           bool small = false) {
     const Variant& v = variants()[variant];
     const int mode = ctx->cfg.score;
     const bool prof = ctx->cfg.profile != 0;
@@ -175,7 +182,7 @@ vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s
     const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[0], s, rec_flags));
     if (levels > 1 && pyramid) {
-        pyr_fn(levels)<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->d_call);
+        pyr_fn(levels)<<<ctx->sm_count * (small ? 1 : 8), 256, 0, s>>>(ctx->d_call);
         VIO_CK(cudaGetLastError());
     }
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[1], s, rec_flags));
@@ -185,10 +192,11 @@ vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s
         VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn[mode], kThreads, v.smem));
         ctx->grid_fused[variant] = std::max(1, occ) * ctx->sm_count;
     }
-    v.fn[mode]<<<ctx->grid_fused[variant], kThreads, v.smem, s>>>(ctx->d_call, ctx->d_counter, ctx->d_status);
+    const int grid = small ? std::min(ctx->grid_fused[variant], ctx->sm_count) : ctx->grid_fused[variant];
+    v.fn[mode]<<<grid, kThreads, v.smem, s>>>(ctx->d_call, ctx->d_counter, ctx->d_status);
     VIO_CK(cudaGetLastError());
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[2], s, rec_flags));
-    decode_kernel<<<ctx->sm_count * 4, 256, 0, s>>>(ctx->d_call, ctx->d_counter);
+    decode_kernel<<<small ? kSmallDecodeCtas : ctx->sm_count * 4, 256, 0, s>>>(ctx->d_call, ctx->d_counter);
     VIO_CK(cudaGetLastError());
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[3], s, rec_flags));
     return VIO_OK;
@@ -196,15 +204,15 @@ vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s
 
 // Graph slot `levels` holds pyramid -> detect -> decode; slot 0 holds
 // detect -> decode alone (the pyramid is already in place).
-vio_status get_graph(vio_ctx* ctx, int variant, int levels, bool pyramid, cudaGraphExec_t* out) {
-    cudaGraphExec_t& g = ctx->graphs[variant][pyramid ? levels : 0];
+vio_status get_graph(vio_ctx* ctx, int variant, int levels, bool pyramid, bool small, cudaGraphExec_t* out) {
+    cudaGraphExec_t& g = ctx->graphs[variant][pyramid ? levels : 0][small ? 1 : 0];
     if (!g) {
         // the launch attributes are set outside the capture
         const Variant& v = variants()[variant];
         VIO_CK(cudaFuncSetAttribute(v.fn[ctx->cfg.score], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
         cudaGraph_t graph = nullptr;
         VIO_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        vio_status es = enqueue_kernels(ctx, variant, levels, ctx->capture_stream, pyramid);
+        vio_status es = enqueue_kernels(ctx, variant, levels, ctx->capture_stream, pyramid, small);
         cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (es != VIO_OK) return es;
         VIO_CK(ce);
@@ -482,6 +490,8 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
         for (int j = 0; j < n_set * n; ++j) so[j] = sweep->outs[j];
     }
 
+    const bool small = acc <= ctx->sm_count && blocks[n] <= 2 * ctx->sm_count &&
+                       cells[n] <= kSmallDecodeCtas * 256 * 4;
     VIO_CK(cudaMemcpyAsync(ctx->d_call, st_base, bytes, cudaMemcpyHostToDevice, s));
     VIO_CK(cudaEventRecord(ctx->ring_ev[slot], s));
     if (sweep) {
@@ -490,9 +500,9 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
             return st;
     } else if (ctx->cfg.use_graphs) {
         cudaGraphExec_t g = nullptr;
-        if ((st = get_graph(ctx, variant, levels, pyramid, &g)) != VIO_OK) return st;
+        if ((st = get_graph(ctx, variant, levels, pyramid, small, &g)) != VIO_OK) return st;
         VIO_CK(cudaGraphLaunch(g, s));
-    } else if ((st = enqueue_kernels(ctx, variant, levels, s, pyramid)) != VIO_OK) {
+    } else if ((st = enqueue_kernels(ctx, variant, levels, s, pyramid, small)) != VIO_OK) {
         return st;
     }
     VIO_CK(cudaEventRecord(ctx->last_ev, s));

@@ -128,8 +128,9 @@ struct vio_ctx {
     cudaStream_t last_stream = nullptr;
     bool have_last = false;
 
-    // one graph per (variant, levels): every batch shape replays it
-    cudaGraphExec_t graphs[8][vio::kMaxLevels + 1] = {};
+    // one graph per (variant, levels, launch shape): every batch shape
+    // replays it; shape 1 is the small-call shape (one CTA per SM at most)
+    cudaGraphExec_t graphs[8][vio::kMaxLevels + 1][2] = {};
     int grid_fused[8] = {};
     int grid_sweep = 0;
     std::unordered_map<ShapeKey, int, ShapeHash> tuned;  // batch shape -> variant
@@ -142,11 +143,12 @@ struct vio_ctx {
 
     void drop_graphs() {
         for (auto& row : graphs)
-            for (auto& g : row)
-                if (g) {
-                    cudaGraphExecDestroy(g);
-                    g = nullptr;
-                }
+            for (auto& pair : row)
+                for (auto& g : pair)
+                    if (g) {
+                        cudaGraphExecDestroy(g);
+                        g = nullptr;
+                    }
     }
 };
 
