@@ -179,10 +179,11 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
  * bytes, at most 4096 bytes between a frame's last pixel and the next
  * frame) are copied as one span by one copy-engine copy (a copy costs about
  * 2 us on top of its bytes, so 64 frames in one buffer upload about 1.5x
- * faster than 64 separate ones); a frame alone in pinned (page-locked)
- * memory with address and pitch multiples of 16 is read by the pyramid
- * kernel through its device mapping, which also writes the device copy of
- * level 0 (one pass over the host link, overlapped with the pyramid); other
+ * faster than 64 separate ones); frames alone in pinned (page-locked)
+ * memory with address and pitch multiples of 16, when a call with more than
+ * one level holds at least 4 of them, are read by the pyramid kernel through
+ * their device mapping, which also writes the device copy of level 0 (one
+ * pass over the host link, overlapped with the pyramid, no copy each); other
  * frames are copied one by one.  Records for pinned, 16-byte aligned
  * host_cells are written in place by the decode kernel; others come back
  * through a staging copy.

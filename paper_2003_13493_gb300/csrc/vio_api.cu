@@ -323,6 +323,8 @@ vio_status enqueue_upload(vio_ctx* ctx, const UploadPlan& p, uint8_t* dst, cudaS
     return VIO_OK;
 }
 
+constexpr int kZeroCopyMin = 4;  // lone pinned frames per call read through their device mapping
+
 // Pyramid (when asked), fused sweep and sweep decode, launched directly.
 vio_status enqueue_sweep(vio_ctx* ctx, int levels, cudaStream_t s, bool pyramid, const SweepInfo* d_sw) {
     const bool prof = ctx->cfg.profile != 0;
@@ -583,10 +585,13 @@ namespace vio {
 
 vio_status detect_from_host(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims, int n, int thresh,
                             int arc, int cell, int levels, int4* const* outs, int32_t* d_counts, cudaStream_t s) {
-    // A frame alone in pinned host memory is read by the pyramid kernel
-    // through its device mapping (it writes the device copy of level 0 as it
-    // goes), so its upload overlaps the pyramid.  Spans of frames that lie
-    // one after another take one copy-engine copy each; so does anything else.
+    // Frames alone in pinned host memory, when a call has at least
+    // kZeroCopyMin of them, are read by the pyramid kernel through their
+    // device mapping (it writes the device copy of level 0 as it goes): their
+    // upload overlaps the pyramid and costs no copy each.  A call with fewer
+    // copies them (the copy engine's latency is lower for a frame or two).
+    // Spans of frames that lie one after another take one copy-engine copy
+    // each; so does anything else.
     const UploadPlan plan = plan_upload(host_frames, dims, n);
     vio_status st;
     if ((st = grow(ctx, (void**)&ctx->d_in, &ctx->in_cap, std::max<size_t>(plan.bytes, 256), false)) != VIO_OK)
@@ -594,7 +599,7 @@ vio_status detect_from_host(vio_ctx* ctx, const uint8_t* const* host_frames, con
     std::vector<const uint8_t*> lev0(n), src0(n, nullptr);
     std::vector<int> src_pitch(n, 0);
     std::vector<bool> skip(plan.copies.size(), false);
-    bool any_up = false;
+    int n_mapped = 0;
     for (int i = 0, c = 0; i < n; c++) {
         const int len = plan.span_len[i];
         const uint8_t* mapped = len == 1 ? static_cast<const uint8_t*>(device_alias(host_frames[i])) : nullptr;
@@ -602,10 +607,12 @@ vio_status detect_from_host(vio_ctx* ctx, const uint8_t* const* host_frames, con
             src0[i] = mapped;
             src_pitch[i] = dims[i].pitch;
             skip[c] = true;
-            any_up = true;
+            ++n_mapped;
         }
         i += len;
     }
+    const bool any_up = n_mapped >= kZeroCopyMin;
+    if (!any_up) std::fill(skip.begin(), skip.end(), false);
     for (int i = 0; i < n; ++i) lev0[i] = ctx->d_in + plan.off[i];
     if ((st = enqueue_upload(ctx, plan, ctx->d_in, s, &skip)) != VIO_OK) return st;
     Upload up;
