@@ -216,7 +216,9 @@ vio_status track_impl(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* c
 
     VIO_CK(cudaMemcpyAsync(T.d_call, hb, bytes, cudaMemcpyHostToDevice, s));
     VIO_CK(cudaEventRecord(T.stage_ev, s));
-    if (L > 1) track_pyr_fn(L)<<<ctx->sm_count * 8, 256, 0, s>>>(T.d_call);
+    // the kernel strides over its grid: a few frames' blocks need no more than one CTA per SM
+    const int pyr_grid = blocks[nf] <= 2 * ctx->sm_count ? ctx->sm_count : ctx->sm_count * 8;
+    if (L > 1) track_pyr_fn(L)<<<pyr_grid, 256, 0, s>>>(T.d_call);
     VIO_CK(cudaGetLastError());
     const int grid = (int)((total + kTrackWarps - 1) / kTrackWarps);
     track_kernel<<<grid, kTrackWarps * 32, 0, s>>>(T.d_call, (uint32_t)off_track);
