@@ -455,13 +455,15 @@ __device__ __forceinline__ uint32_t coarse8(uint32_t C, uint32_t L, uint32_t R, 
 //   1. TMA loads the region plus the 3-pixel circle halo (box 144 x TH+2R+6)
 //      into one of two image buffers; the other buffer is loading the next
 //      item meanwhile.
-//   2. Coarse test on every score-region pixel, 8 pixels per lane, pixels
-//      outside the testable area masked off; each warp appends the kept
-//      pixels of each of its row pairs to its own queue (warp scan).
+//   2. Coarse test on every score-region pixel, 8 pixels per lane (the
+//      compass rule on level 0, the 8-point rule above it), pixels outside
+//      the testable area masked off; each warp appends the kept pixels of
+//      each of its row pairs to its own queue (warp scan).
 //   3. Each warp runs the full segment test on its queue and compacts the
 //      corners in place, then scores the corners and writes the scores into
 //      the score tile.
-//   4. After a barrier of the consumer warps (NMS reads other warps' rows),
+//   4. Once its two neighbouring warps have written their scores (the NMS
+//      reads up to R rows of theirs; per-warp mbarriers, see neighbours_wait),
 //      (2R+1)x(2R+1) NMS on the corner lists; when a warp's survivors share one cell
 //      their packed keys are max-reduced with __reduce_max_sync and folded
 //      into the global cell key with one atomicMax, otherwise each survivor
