@@ -85,3 +85,26 @@ def test_track_defaults_and_null_context(lib):
     assert (p.levels, p.patch_fine, p.patch_coarse, p.max_iters, p.model) == (3, 16, 8, 30, 3)
     assert abs(p.min_update - 0.01) < 1e-7
     assert lib.vio_track(None, None, None, None, 0, None, None, None, None, None) == 1
+
+
+def test_host_batch_marshals_once_and_checks_buffers():
+    """HostBatch (host logic only): dims and pointers are taken from the
+    arrays once; wrong dtypes, layouts or output counts are refused."""
+    import numpy as np
+
+    frames = [np.zeros((480, 640), np.uint8), np.zeros((720, 1280), np.uint8)[:, :1000]]
+    outs = [np.zeros((vio.num_cells(f.shape[1], f.shape[0], 32), 4), np.int32) for f in frames]
+    counts = np.zeros(2, np.int32)
+    b = vio.HostBatch(frames, outs, counts)
+    assert b.n == 2
+    assert [(d.w, d.h, d.pitch) for d in b.dims] == [(640, 480, 640), (1000, 720, 1280)]
+    assert [b.fptr[i] for i in range(2)] == [f.ctypes.data for f in frames]
+    assert [b.optr[i] for i in range(2)] == [o.ctypes.data for o in outs]
+    assert b.cptr.value == counts.ctypes.data
+    assert vio.HostBatch(frames, outs).cptr is None
+    with pytest.raises(ValueError):
+        vio.HostBatch([np.zeros((8, 8), np.int16)], outs[:1])
+    with pytest.raises(ValueError):
+        vio.HostBatch([np.zeros((8, 8, 2), np.uint8)[:, :, 0]], outs[:1])  # column stride 2
+    with pytest.raises(ValueError):
+        vio.HostBatch(frames, outs[:1])
