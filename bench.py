@@ -163,7 +163,8 @@ def recorded_profile(workload: str, kernel: str = "fast_nms_cell") -> dict:
     vals = {}
     with open(path) as f:
         for line in f:
-            for key in ("kernel_source_sha256", "dram_bytes_per_launch", "alu_pipe_pct", "issue_active_pct"):
+            for key in ("kernel_source_sha256", "dram_bytes_per_launch", "alu_pipe_pct", "issue_active_pct",
+                        "warp_instructions_per_launch"):
                 if line.startswith(key + ":"):
                     vals[key] = line.split(":", 1)[1].split()[0].strip()
     if vals.get("kernel_source_sha256") != kernel_source_hash(kernel):
@@ -377,6 +378,18 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_extras:
         res.update(extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cptr, n, mpx,
                           ms_per_step))
+        alu = res.get("roofline", {}).get("alu", {})
+        kern_ms = res.get("stage_ms", {}).get(res["roofline"]["kernel"].replace("_kernel", "")) if alu else None
+        if "warp_instructions_per_launch" in alu and kern_ms and (clk or {}).get("sm_mhz"):
+            # the issue roofline: warp instructions the kernel executes (ncu, same
+            # source) over its live duration, against one instruction per cycle
+            # per scheduler (4 per SM) at the SM clock sampled under load
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            ach = alu["warp_instructions_per_launch"] / (kern_ms * 1e-3) / 1e9
+            pk = sms * 4 * clk["sm_mhz"] * 1e6 / 1e9
+            alu["issue"] = {"achieved": round(ach, 1), "peak": round(pk, 1), "unit": "G warp instructions/s",
+                            "frac": round(ach / pk, 4),
+                            "peak_from": f"{sms} SMs x 4 schedulers x 1 instruction/cycle x {clk['sm_mhz']:.0f} MHz"}
     det.close()
     return res
 
@@ -521,6 +534,8 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
                                   "binds": "integer issue: the ALU pipe is this busy while DRAM moves the "
                                            "algorithmic bytes at the HBM fraction above",
                                   "source": f"profiles/{kname.replace('_kernel', '')}_{args.workload}.md"}
+        if "warp_instructions_per_launch" in prof_vals:
+            out["roofline"]["alu"]["warp_instructions_per_launch"] = int(prof_vals["warp_instructions_per_launch"])
     out["stage_ms"] = {"pyramid": round(stage[0], 5), kname.replace("_kernel", ""): round(stage[1], 5),
                        "decode": round(stage[2], 5)}
     step_gbs = step_bytes / (ms_per_step * 1e-3) / 1e9
