@@ -457,6 +457,20 @@ def e2e_leg(args, wl, det, dev, stream, frames_np, dims, n, world) -> dict:
     packed_async, packed_sync = rates([v.numpy() for v in packed])
     sep_async, sep_sync = rates([t.numpy() for t in separate])
     e2e_det.close()
+    # the host link's rate for one copy of the whole buffer: the bound of the
+    # pipelined path
+    dst = torch.empty(arena.numel(), dtype=torch.uint8, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    with torch.cuda.stream(stream):
+        for _ in range(6):
+            e0.record(stream)
+            dst.copy_(arena, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+    link_gbs = arena.numel() / (best * 1e-3) / 1e9
+    e2e_gbs = packed_async / world * arena.numel() / n / 1e9
     # bytes of one job step: every rank copies its own frames and records
     h2d = world * sum(w * h for w, h in dims)
     d2h = world * (sum(16 * vio.num_cells(w, h, wl["cell"]) for w, h in dims) + 4 * n)
@@ -468,6 +482,10 @@ def e2e_leg(args, wl, det, dev, stream, frames_np, dims, n, world) -> dict:
                     "(vio.HostBatch), one C call per step",
             "sync": {"value": packed_sync, "unit": "frames/s",
                      "what": "vio_detect_host, one synchronous call per step, same buffer"},
+            "host_link": {"achieved_gbs": round(e2e_gbs, 1), "one_copy_gbs": round(link_gbs, 1),
+                          "frac": round(e2e_gbs / link_gbs, 3),
+                          "what": "frame bytes uploaded per second by the pipelined path, against one "
+                                  "cudaMemcpyAsync of the same pinned buffer timed alone"},
             "separate_frames": {"value": sep_async, "sync": sep_sync, "unit": "frames/s",
                                 "what": "each frame in its own pinned allocation: one copy per frame when "
                                         "pipelined; read by the pyramid kernel through its device mapping "
