@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/profile legs")
     ap.add_argument("--spin", type=float, default=0.5, help="seconds of untimed steps before timing")
     ap.add_argument("--variant", type=int, default=-1, help="pin a tile variant instead of autotuning")
+    ap.add_argument("--cell", type=int, default=0, help="pin the cell size instead of the workload's choice")
     ap.add_argument("--no-tracker", action="store_true", help="skip the feature-tracker leg")
     ap.add_argument("--tracker-only", action="store_true",
                     help="run only the feature-tracker leg and print its JSON object")
@@ -268,7 +269,9 @@ def run_ours(args, rank, world, local_rank):
 
     from paper_2003_13493_gb300 import vio
 
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.cell:
+        wl["cell"] = args.cell
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     frames_np = make_frames(args.workload)
@@ -965,7 +968,9 @@ def serving_leg(args, dev_index: int) -> dict:
 
 
 def run_reference(args, rank, world):
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.cell:
+        wl["cell"] = args.cell
     frames = make_frames(args.workload)
     if rank != 0:
         return None
