@@ -547,6 +547,13 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
                        "frac": round(achieved / peak, 4), "traffic": traffic,
                        "kernel": kname, "peak_kind": f"{kind} hbm_gbs",
                        "algorithmic_bytes_per_launch": int(fused_bytes)}
+    # where `traffic` comes from: not measured in this run, but read from the
+    # committed ncu summary of the same kernel source (matched by hash); null
+    # when the source changed since that capture
+    out["roofline"]["traffic_source"] = {
+        "profile": f"profiles/{kname.replace('_kernel', '')}_{args.workload}.md",
+        "kernel_source_sha256": kernel_source_hash(kname.replace("_kernel", "")),
+        "matched": traffic is not None}
     prof_vals = recorded_profile(args.workload, kname.replace("_kernel", ""))
     if "alu_pipe_pct" in prof_vals:
         # what binds instead: integer issue (ncu on the same kernel source)

@@ -147,8 +147,11 @@ size_t vio_num_cells(int w, int h, int cell_size);
  *   out_counts DEVICE int32[n_frames] receiving the number of non-empty
  *              cells per frame, or NULL.
  *
- * Each frame must satisfy 7 <= w, 7 <= h and w * h < 2^28.  Asynchronous
- * on `stream`.  Errors: VIO_ERR_INVALID_ARG, VIO_ERR_OOM, VIO_ERR_CUDA.
+ * Each frame must satisfy 7 <= w <= 65535, 7 <= h <= 65535 and
+ * w * h < 2^28 (the kernels find a level pixel's cell with a multiply-high
+ * that is exact for level coordinates below 2^16; larger frames return
+ * VIO_ERR_INVALID_ARG).  Asynchronous on `stream`.  Errors:
+ * VIO_ERR_INVALID_ARG, VIO_ERR_OOM, VIO_ERR_CUDA.
  */
 vio_status vio_detect(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims* dims, int n_frames,
                       int thresh, int arc_len, int cell_size, int levels,
@@ -165,7 +168,8 @@ vio_status vio_detect(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims
  *                         of detection p
  *   out_counts            DEVICE int32[n_params * n_frames] (same order) or NULL
  *
- * Other arguments, checks and errors as vio_detect.  Asynchronous on `stream`.
+ * Other arguments, checks and errors as vio_detect (7 <= w, h <= 65535,
+ * w * h < 2^28).  Asynchronous on `stream`.
  */
 vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims* dims, int n_frames,
                             const int* thresholds, const int* arc_lens, int n_params, int cell_size, int levels,
@@ -186,7 +190,8 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
  * pass over the host link, overlapped with the pyramid, no copy each); other
  * frames are copied one by one.  Records for pinned, 16-byte aligned
  * host_cells are written in place by the decode kernel; others come back
- * through a staging copy.
+ * through a staging copy.  Frame sizes and the other arguments are checked
+ * as by vio_detect (7 <= w, h <= 65535, w * h < 2^28).
  */
 vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims,
                            int n_frames, int thresh, int arc_len, int cell_size, int levels,
@@ -209,8 +214,9 @@ vio_status vio_detect_host(vio_ctx* ctx, const uint8_t* const* host_frames, cons
  *                device; they must not be read or reused before completion
  *   host_counts  PINNED host int32[n_frames] or NULL
  *
- * Errors: VIO_ERR_INVALID_ARG (as vio_detect, or host_cells / host_counts not
- * pinned), VIO_ERR_OOM, VIO_ERR_CUDA.
+ * Errors: VIO_ERR_INVALID_ARG (as vio_detect, including 7 <= w, h <= 65535
+ * and w * h < 2^28, or host_cells / host_counts not pinned), VIO_ERR_OOM,
+ * VIO_ERR_CUDA.
  */
 vio_status vio_detect_host_async(vio_ctx* ctx, const uint8_t* const* host_frames, const vio_dims* dims,
                                  int n_frames, int thresh, int arc_len, int cell_size, int levels,
@@ -296,7 +302,8 @@ vio_status vio_serve_start(vio_ctx* ctx, const vio_serve_config* cfg);
 /* Queues one frame.  host_frame must stay valid and unchanged until the
  * frame completes (pinned memory lets its copy overlap other work).
  * *ticket identifies the frame for vio_poll.  Errors: VIO_ERR_INVALID_ARG
- * (not serving, bad dims), VIO_ERR_BUSY (queue full), VIO_ERR_OOM (frame
+ * (not serving, or dims outside vio_detect's limits: 7 <= w, h <= 65535,
+ * w * h < 2^28, pitch >= w), VIO_ERR_BUSY (queue full), VIO_ERR_OOM (frame
  * larger than the budget), or the scheduler's own error. */
 vio_status vio_submit(vio_ctx* ctx, int stream_id, const uint8_t* host_frame, vio_dims dims, uint64_t* ticket);
 
@@ -328,7 +335,8 @@ vio_status vio_serve_stop(vio_ctx* ctx);
  * keeps on every device that loads it, until the process exits.
  *
  *   frame      DEVICE pointer, 16-byte aligned, dims.pitch a multiple of 16
- *   dims       as vio_detect; the frame must fit the array:
+ *   dims       as vio_detect (7 <= w, h <= 65535); the frame must also fit
+ *              the array:
  *              4096 + 8 * cells (rounded up to 256)
  *              + sum over k >= 1 of round_up(w >> k, 128) * (h >> k),
  *              each level rounded up to 256, must not exceed
@@ -345,9 +353,11 @@ vio_status vio_serve_stop(vio_ctx* ctx);
  * calls that overlap on the GPU (another stream, another host thread) race
  * and must be serialised by the caller.  The first call on each device sets
  * up that device (it looks up the array's device address, with the device
- * current); make that first call before any stream capture.  A bounded
- * device-side wait that expires is not reported here (use vio_detect and
- * vio_sync where that matters).  Errors: VIO_ERR_INVALID_ARG,
+ * current); make that first call before any stream capture.  The device-side
+ * checks are not reported here: a bounded wait that expires, or a decoded
+ * cell key that lies outside its cell, is recorded in the array's status
+ * word, which this entry point never reads back (use vio_detect and vio_sync
+ * where that matters).  Errors: VIO_ERR_INVALID_ARG,
  * VIO_ERR_UNSUPPORTED (not an sm_103 device), VIO_ERR_CUDA.
  */
 #define VIO_NOALLOC_SCRATCH_BYTES (4u << 20)

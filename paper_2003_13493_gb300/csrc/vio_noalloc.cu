@@ -16,11 +16,14 @@
 #include <mutex>
 
 #include "../../include/vio.h"
-// This translation unit instantiates the kernels again; the one kernel that
-// is not a template gets a local name so the two copies do not collide.
-#define decode_kernel noalloc_decode_kernel
+// This translation unit compiles the kernels of vio_kernels.cuh a second
+// time.  decode_kernel is static, so each unit launches its own copy; the
+// template kernels' host stubs, however, are merged by the linker, so a
+// launch from here may run the copy registered by another unit (and the
+// other way round).  That is only correct while vio_kernels.cuh keeps no
+// file-scope __device__ or __constant__ state: its kernels must read
+// everything from their arguments.
 #include "vio_kernels.cuh"
-#undef decode_kernel
 
 using namespace vio;
 
@@ -39,10 +42,13 @@ constexpr size_t kCountOff = 2048;  // work counter, then status word
 constexpr size_t kKeysOff = 4096;   // cell keys, then the pyramid levels
 
 // Largest call block for one frame: header, one frame descriptor, one
-// level-0 map, kMaxLevels - 1 level maps, three small prefix tables.
-struct NoallocBlock {
+// level-0 map, kMaxLevels - 1 level maps, three small prefix tables.  The
+// sections start at multiples of 128 bytes and hold pointers and tensor maps
+// (aligned like CUtensorMap), so the block itself is aligned like a tensor map.
+struct alignas(alignof(CUtensorMap)) NoallocBlock {
     uint8_t bytes[kCallCap];
 };
+static_assert(alignof(NoallocBlock) >= alignof(CUtensorMap), "tensor maps inside the block stay aligned");
 
 __global__ void noalloc_load_call(const __grid_constant__ NoallocBlock blk, uint8_t* __restrict__ dst, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = blk.bytes[i];
@@ -205,6 +211,9 @@ extern "C" vio_status vio_detect_noalloc(const uint8_t* frame, vio_dims d, int t
     hdr->cell = cell;
     hdr->tile_h = kTH;
     hdr->counts = out_count;
+    // the decode's cell-key check reports into the scratch status word too
+    // (cleared below with the counter); this entry point does not read it back
+    hdr->status = status;
     hdr->off_fds = (uint32_t)off_fds;
     hdr->off_maps0 = (uint32_t)off_maps0;
     hdr->off_mapsk = (uint32_t)off_mapsk;
@@ -253,6 +262,6 @@ extern "C" vio_status vio_detect_noalloc(const uint8_t* frame, vio_dims d, int t
     noalloc_load_call<<<1, 256, 0, s>>>(blk, base + kCallOff, (int)bytes);
     if (levels > 1) pyr_fn(levels)<<<S->sm_count * 8, 256, 0, s>>>(base + kCallOff);
     fused_fn(score)<<<S->grid_fused[score], kThreads, TileGeom<kTH>::SMEM, s>>>(base + kCallOff, counter, status);
-    noalloc_decode_kernel<<<S->sm_count * 4, 256, 0, s>>>(base + kCallOff, counter);
+    decode_kernel<<<S->sm_count * 4, 256, 0, s>>>(base + kCallOff, counter);
     return cudaGetLastError() == cudaSuccess ? VIO_OK : VIO_ERR_CUDA;
 }

@@ -205,6 +205,29 @@ def test_maximum_frame_size_sampled(dets):
         dets[0].detect([too_big], 15, 9, 64, 3)
 
 
+@pytest.mark.parametrize("levels", [1, 2])
+def test_width_limit(dets, levels):
+    """Frames at the width limit: level x coordinates close to 2^16, where
+    the cell index of a level pixel (a multiply-high by ceil(2^32 / C_k)) is
+    still exact; a frame one pixel wider is rejected."""
+    W, H = 65528, 64
+    base = synth.make_frame(4096, 64, seed=321, n_shapes=24)
+    img = np.ascontiguousarray(np.tile(base, (1, 16))[:, :W])
+    got, cnt = run(dets[0], [img], 15, 9, 32, levels)
+    assert_parity(got, cnt, [img], 15, 9, 32, levels, 0)
+    # the last column of cells has features: x near 2^16 is exercised
+    last = got[0].reshape(-1, (W + 31) // 32, 4)[:, -4:]
+    assert (last[..., 2] >= 0).any()
+    for w in (65535, 65536):
+        frame = torch.zeros((16, w), dtype=torch.uint8, device="cuda")
+        if w <= 65535:
+            dets[0].detect([frame], 15, 9, 32, 1)
+            dets[0].sync()
+        else:
+            with pytest.raises(vio.VioError):
+                dets[0].detect([frame], 15, 9, 32, 1)
+
+
 def test_large4k_sweep_full_launch_sampled(dets):
     """The 4K sweep exactly as the benchmark launches it: all 32 frames of
     3840x2160 (seeds 100..131, 400 shapes), 4 levels, 64x64 cells, the 8

@@ -101,8 +101,9 @@ def test_patch_sizes_and_levels(det, fine, coarse, levels):
 
 def test_default_parameters_with_early_exit(det):
     # the early exit compares |dt| with min_update in fp32 on the GPU and
-    # fp64 in the oracle, so an iteration count may differ by one near the
-    # threshold; positions then differ by less than min_update
+    # fp64 in the oracle, so a level's iteration count may differ by one near
+    # the threshold: at most one per level, 3 in total over these 3 levels;
+    # positions then differ by less than min_update
     prev = synth.smooth_frame(752, 480, seed=13)
     nxt = synth.smooth_frame(752, 480, seed=13, dx=0.4, dy=1.9, gain=1.1, offset=-6.0)
     pts = grid(752, 480, 29, 40)

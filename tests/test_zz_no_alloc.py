@@ -18,13 +18,13 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _noalloc(lib, frame, thresh, arc, cell, levels, score=0):
+def _noalloc(lib, frame, thresh, arc, cell, levels, score=0, with_count=True):
     h, w = frame.shape
     out = torch.full((vio.num_cells(w, h, cell), 4), 7, dtype=torch.int32, device="cuda")
     cnt = torch.full((1,), -5, dtype=torch.int32, device="cuda")
     st = lib.vio_detect_noalloc(ctypes.c_void_p(frame.data_ptr()), vio.Dims(w, h, frame.stride(0)), thresh, arc,
                                 cell, levels, score, ctypes.c_void_p(out.data_ptr()),
-                                ctypes.c_void_p(cnt.data_ptr()),
+                                ctypes.c_void_p(cnt.data_ptr() if with_count else None),
                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     return st, out, cnt
 
@@ -55,6 +55,42 @@ def test_noalloc_matches_vio_detect_on_consecutive_calls():
             ref, n = _reference(f, thresh, arc, cell, levels, score)
             assert np.array_equal(out.cpu().numpy(), ref), (w, h)
             assert int(cnt[0]) == n
+
+
+def _strided(w, h, seed, pad):
+    """A frame seen through a row-strided view: pitch w + pad bytes."""
+    full = torch.zeros((h, w + pad), dtype=torch.uint8, device="cuda")
+    full[:, :w] = torch.from_numpy(synth.make_frame(w, h, seed=seed)).cuda()
+    return full[:, :w]
+
+
+# branches the cases above leave out: one level (no pyramid launch, no level
+# maps), the SAD-A score, a pitch larger than the width, and no count output
+BRANCH_CASES = [
+    dict(w=752, h=480, seed=0, thresh=10, arc=9, cell=32, levels=1, score=0, pad=0, with_count=True),
+    dict(w=752, h=480, seed=5, thresh=20, arc=10, cell=32, levels=3, score=1, pad=0, with_count=True),
+    dict(w=752, h=480, seed=6, thresh=15, arc=9, cell=64, levels=3, score=0, pad=64, with_count=True),
+    dict(w=640, h=480, seed=7, thresh=15, arc=9, cell=32, levels=2, score=0, pad=0, with_count=False),
+]
+
+
+@pytest.mark.parametrize("case", BRANCH_CASES, ids=["one-level", "sad-a", "strided", "no-count"])
+def test_noalloc_branches_match_vio_detect(case):
+    lib = vio.load()
+    c = dict(case)
+    frames = [_strided(c["w"], c["h"], c["seed"] + j, c["pad"]) for j in range(2)]
+    assert frames[0].stride(0) == c["w"] + c["pad"]
+    results = [_noalloc(lib, f, c["thresh"], c["arc"], c["cell"], c["levels"], c["score"], c["with_count"])
+               for f in frames]
+    torch.cuda.synchronize()
+    for f, (st, out, cnt) in zip(frames, results):
+        assert st == 0, (c, st)
+        ref, n = _reference(f, c["thresh"], c["arc"], c["cell"], c["levels"], c["score"])
+        assert np.array_equal(out.cpu().numpy(), ref), c
+        if c["with_count"]:
+            assert int(cnt[0]) == n
+        else:
+            assert int(cnt[0]) == -5  # no count pointer: nothing written there
 
 
 def test_noalloc_rejects_frames_beyond_the_array():
