@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--variant", type=int, default=-1, help="pin a tile variant instead of autotuning")
     ap.add_argument("--cell", type=int, default=0, help="pin the cell size instead of the workload's choice")
     ap.add_argument("--no-tracker", action="store_true", help="skip the feature-tracker leg")
+    ap.add_argument("--no-large4k", action="store_true", help="skip the 4K sweep leg of the default run")
     ap.add_argument("--tracker-only", action="store_true",
                     help="run only the feature-tracker leg and print its JSON object")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
@@ -645,6 +646,9 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     out["latency"] = latency_leg(args, dev.index)
     if args.serve_seconds > 0:
         out["serving"] = serving_leg(args, dev.index)
+        out["serving_saturation"] = serving_saturation_leg(args, dev.index)
+    if args.workload == "mixed64" and not args.no_large4k:
+        out["large4k"] = large4k_leg(args, dev.index)
     if not args.no_tracker:
         out["tracker"] = tracker_leg(args, dev.index)
 
@@ -965,6 +969,8 @@ def serving_leg(args, dev_index: int) -> dict:
     out = {"value": round(served["frames_per_s"], 1), "unit": "frames/s", "offered_fps": round(offered, 1),
            "frames": len(events), "p50_us": round(served["p50_us"], 1), "p99_us": round(served["p99_us"], 1),
            "max_us": round(served["max_us"], 1), "mean_batch": round(served["mean_batch"], 2),
+           "max_batch_frames": int(served["max_batch_frames"]), "max_lanes_in_flight": int(served["max_lanes_in_flight"]),
+           "overlapped_batches": int(served["overlapped_batches"]), "batches": int(served["batches"]),
            "max_submit_lag_us": served["max_submit_lag_us"], "lanes": 3, "max_batch": 32,
            "plain": {"value": round(plain["frames_per_s"], 1), "p50_us": round(plain["p50_us"], 1),
                      "p99_us": round(plain["p99_us"], 1), "max_us": round(plain["max_us"], 1),
@@ -972,6 +978,104 @@ def serving_leg(args, dev_index: int) -> dict:
            "what": f"{n_streams} Poisson camera streams (200..1000 Hz) for {T:g} s, 4 GiB budget, "
                    "latency from submit to cells in host memory"}
     return out
+
+
+def large4k_leg(args, dev_index: int) -> dict:
+    """The 4K sweep workload (32 frames of 3840x2160, 4 levels, FAST-12 and
+    FAST-9 at thresholds 5..40, 64x64 cells) timed like the main line: its own
+    warm-up, timed steps on the device, clocks and the roofline of the fused
+    sweep kernel.  The 265 MB batch is larger than L2."""
+    import copy
+
+    a = copy.copy(args)
+    a.workload, a.cell, a.variant = "large4k", 0, -1
+    a.steps, a.warmup, a.spin = max(4, min(args.steps, 12)), 3, 0.3
+    a.no_extras, a.no_cpu_baseline, a.no_large4k = False, True, True
+    r = run_ours(a, 0, 1, dev_index)
+    keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "mpixel_per_s", "detections_per_s",
+            "config", "clocks", "gpu_launches", "roofline", "stage_ms", "step_roofline")
+    return {k: r[k] for k in keep if k in r}
+
+
+def serving_saturation_leg(args, dev_index: int) -> dict:
+    """The serving mix of serving_leg with its Poisson rates scaled up until
+    one lane at one frame per launch saturates, and past it.  At each rate
+    the batching server (3 lanes, up to 32 frames per launch) and the plain
+    one (1 lane, 1 frame per launch) see the same arrivals; each run lasts
+    `seconds` of arrivals (the plain server's backlog then drains)."""
+    import numpy as np
+    import torch
+
+    from paper_2003_13493_gb300 import synth, vio
+
+    n_streams, per_stream = 16, 4
+    seconds = max(0.5, min(2.0, args.serve_seconds / 5))
+    pools = []
+    for s in range(n_streams):
+        w, h = synth.MIXED_SIZES[s % 4]
+        pools.append([torch.from_numpy(synth.make_frame(w, h, seed=5000 + 16 * s + j)).pin_memory()
+                      for j in range(per_stream)])
+    dims = [[vio.Dims(p.shape[1], p.shape[0], p.shape[1]) for p in pool] for pool in pools]
+    ptrs = [[p.data_ptr() for p in pool] for pool in pools]
+
+    def schedule(scale, seed):
+        rng = np.random.default_rng(seed)
+        ev = []
+        for s in range(n_streams):
+            lam = scale * (200.0 + 800.0 * s / (n_streams - 1))
+            t = rng.exponential(1.0 / lam)
+            j = 0
+            while t < seconds:
+                ev.append((t, s, j % per_stream))
+                t += rng.exponential(1.0 / lam)
+                j += 1
+        ev.sort()
+        return ev
+
+    def run(events, **kw):
+        det = vio.Detector(device=dev_index, max_frames=max(64, kw.get("max_batch", 1)))
+        cfg = dict(thresh=15, arc_len=9, cell_size=32, levels=3, keep_results=0, mem_budget_bytes=4 << 30,
+                   queue_capacity=1 << 22, **kw)
+        det.serve_start(**cfg)
+        for s in range(n_streams):
+            det.submit_raw(s, ptrs[s][0], dims[s][0])
+        det.drain(120000)
+        det.serve_stop()
+        det.serve_start(**cfg)
+        lag = 0.0
+        rejected = 0
+        t0 = time.perf_counter()
+        for (t, s, j) in events:
+            while True:
+                now = time.perf_counter() - t0
+                if now >= t:
+                    break
+            lag = max(lag, now - t)
+            st, _ = det.submit_raw(s, ptrs[s][j], dims[s][j])
+            rejected += st != 0
+        det.drain(600000)
+        st = det.serve_stats()
+        det.serve_stop()
+        det.close()
+        return {"frames_per_s": round(st["frames_per_s"], 1), "p50_us": round(st["p50_us"], 1),
+                "p99_us": round(st["p99_us"], 1), "mean_batch": round(st["mean_batch"], 2),
+                "max_batch_frames": int(st["max_batch_frames"]), "max_lanes_in_flight": int(st["max_lanes_in_flight"]),
+                "overlapped_batches": int(st["overlapped_batches"]), "batches": int(st["batches"]),
+                "rejected": rejected, "max_submit_lag_us": round(lag * 1e6, 1)}
+
+    points = []
+    for scale in (1, 4, 16, 48):
+        ev = schedule(scale, 40 + scale)
+        offered = len(ev) / seconds
+        served = run(ev, max_batch=32, lanes=3, max_wait_us=0)
+        plain = run(ev, max_batch=1, lanes=1, max_wait_us=0)
+        points.append({"rate_scale": scale, "offered_fps": round(offered, 1), "frames": len(ev),
+                       "served": served, "plain": plain})
+    return {"points": points, "seconds_of_arrivals": seconds,
+            "what": "the 16-stream serving mix with every stream's Poisson rate multiplied by rate_scale; "
+                    "served = 3 lanes, up to 32 frames per launch; plain = 1 lane, 1 frame per launch; "
+                    "frames/s = completed frames / (last completion - first submit); latency from submit "
+                    "to cells in host memory"}
 
 
 def run_reference(args, rank, world):

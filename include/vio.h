@@ -59,7 +59,7 @@
 extern "C" {
 #endif
 
-#define VIO_ABI_VERSION 1
+#define VIO_ABI_VERSION 2
 #define VIO_MAX_LEVELS 5
 
 typedef struct vio_ctx vio_ctx;
@@ -290,6 +290,12 @@ typedef struct {
     double mean_batch;      /* frames per launch                                             */
     double p50_us, p99_us, max_us, mean_us; /* submit -> cells in host memory, per frame      */
     double frames_per_s;    /* completed frames / (last completion - first submit)           */
+    /* evidence of batching and overlap: */
+    uint64_t max_batch_frames;   /* most frames one launch carried                           */
+    uint64_t max_lanes_in_flight;/* most lanes with a launched, not yet retired batch at once */
+    uint64_t overlapped_batches; /* batches whose device-time interval (CUDA events around the
+                                    lane's work: upload, kernels, result copy) overlapped the
+                                    interval of a batch on another lane                       */
 } vio_serve_stats_t;
 
 /* Defaults: thresh 15, arc 9, cell 32, levels 3, batch 32, no wait, 3 lanes,

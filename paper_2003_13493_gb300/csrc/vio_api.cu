@@ -233,8 +233,8 @@ struct Upload {
     const int* pitch = nullptr;
 };
 
-// Up to kMaxSweep settings detected by one fused sweep launch (thresholds
-// non-decreasing); outs[s * n + i] receives frame i of setting s.
+// Up to kMaxSweep settings detected by one fused sweep launch (ordered by
+// arc length); outs[s * n + i] receives frame i of setting s.
 struct SweepSpec {
     int n_set = 0;
     int thresh[kMaxSweep] = {};
@@ -864,11 +864,17 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
     }
     ctx->last_variant = vi;
     if (ctx->cfg.score == VIO_SCORE_SAD_B && ctx->cfg.nms_radius == 1 && n_params > 1) {
-        // fused sweep: settings sorted by threshold, up to kMaxSweep per launch,
-        // the pyramid built by the first launch
+        // fused sweep: settings grouped by threshold, up to kMaxSweep per
+        // launch (the coarse test runs at a group's lowest threshold), each
+        // group ordered by arc length so that settings of one arc length
+        // share the kernel's window minima; the pyramid is built by the first
+        // launch
         std::vector<int> order(n_params);
         for (int p = 0; p < n_params; ++p) order[p] = p;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return thresholds[a] < thresholds[b]; });
+        for (int g0 = 0; g0 < n_params; g0 += kMaxSweep)
+            std::stable_sort(order.begin() + g0, order.begin() + std::min(n_params, g0 + kMaxSweep),
+                             [&](int a, int b) { return arc_lens[a] < arc_lens[b]; });
         std::vector<int4*> outs((size_t)kMaxSweep * n);
         const int v0 = first_variant(1);
         for (int g0 = 0; g0 < n_params; g0 += kMaxSweep) {

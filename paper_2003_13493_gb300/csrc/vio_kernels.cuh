@@ -233,6 +233,15 @@ __device__ __forceinline__ uint32_t rotl16(uint32_t m, int s) {
     return ((m << s) | (m >> (16 - s))) & 0xFFFFu;
 }
 
+// [sign(a byte 1), sign(a byte 3), sign(b byte 1), sign(b byte 3)]: each result
+// byte is 0xFF when the bit 15 / bit 31 it is taken from is set, else 0x00
+// (the PTX byte permute with the sign-replicate bit set in every selector).
+__device__ __forceinline__ uint32_t prmt_sign_flags(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, 0xFDB9;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
 // Four bytes packed into one word, byte 0 first.
 __device__ __forceinline__ uint32_t pack4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     return __byte_perm(__byte_perm(a, b, 0x0040), __byte_perm(c, d, 0x0040), 0x5410);
@@ -307,8 +316,13 @@ __device__ __forceinline__ uint32_t mt_score(const uint32_t (&v)[16], uint32_t c
 // when v > c + t (brighter), and the high lane is 0x7FFF + (c - t) - v,
 // whose bit 31 is set exactly when v < c - t (darker).  Neither lane leaves
 // its 16 bits, so the two compares are exact for all v, c in 0..255 and
-// t in 0..255.  Shifting the flags down point by point gives the 16-bit
-// bright mask in bits 0..15 and the dark mask in bits 16..31, bit i = point i.
+// t in 0..255.  The flags become masks in two steps: a byte permute with
+// sign replication turns the flag bits (bits 15 and 31 are the sign bits of
+// bytes 1 and 3) of points i and i + 8 into four 0x00 / 0xFF bytes
+// [bright_i, dark_i, bright_i+8, dark_i+8]; keeping bit i of each byte and
+// OR-ing the eight words gives bright 0..7, dark 0..7, bright 8..15 and
+// dark 8..15 in bytes 0..3; a last permute orders them as the 16-bit bright
+// mask in bits 0..15 and the dark mask in bits 16..31, bit i = point i.
 template <int MODE, int P, bool SCORE = true>
 __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, int t, int n) {
     const uint32_t c = p[0];
@@ -316,15 +330,13 @@ __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, i
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * P + circ_dx(i)];
     const uint32_t K = ((0x7FFFu - c - (uint32_t)t) & 0xFFFFu) | ((0x7FFFu + c - (uint32_t)t) << 16);
-    // four independent chains (points i = 4j + q, q = 0..3) shifted by 4
-    // per step leave point i's flags at bits i + 3 - q, merged below
-    uint32_t a[4] = {0u, 0u, 0u, 0u};
+    uint32_t w[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const uint32_t w = K + v[i] * 0xFFFF0001u;
-        a[i & 3] = (a[i & 3] >> 4) | (w & 0x80008000u);
-    }
-    const uint32_t acc = (a[0] >> 3) | (a[1] >> 2) | (a[2] >> 1) | a[3];
+    for (int i = 0; i < 16; ++i) w[i] = K + v[i] * 0xFFFF0001u;
+    uint32_t bytes = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) bytes |= prmt_sign_flags(w[i], w[i + 8]) & (0x01010101u << i);
+    const uint32_t acc = __byte_perm(bytes, 0u, 0x3120);
     const uint32_t bm = acc & 0xFFFFu, dm = acc >> 16;
     // at most one polarity can hold n >= 9 points
     const bool bright = __popc(bm) >= n;
@@ -374,75 +386,17 @@ __device__ __forceinline__ uint32_t sad_b(const uint8_t* __restrict__ p) {
     return s;
 }
 
-// Coarse test (the CCRF of Algorithm 1) for the 4 pixels of one shared-memory
-// word.  An arc of n >= 9 contiguous points contains floor(n/4) >= 2
-// cyclically consecutive compass points (0, 4, 8, 12), all of them darker or
-// brighter and therefore all with |I_x - I_c| > t.  The test keeps a pixel
-// when two adjacent compass points (n <= 11) or three of the four (n >= 12)
-// differ from the centre by more than t, so it never drops a corner.
-//   C, L, R: the word and its left/right neighbours in the centre row;
-//   N, S: the words 3 rows up and down.
-// Returns bit 7 of byte j set for each kept pixel j.  k7 and the branch on
-// t >= 128 implement the byte-wise compare d > t exactly (see below).
-template <bool HIGH_T, bool THREE>
-__device__ __forceinline__ uint32_t coarse4(uint32_t C, uint32_t L, uint32_t R, uint32_t N, uint32_t S,
-                                            uint32_t k7) {
-    const uint32_t E = __byte_perm(C, R, 0x6543);  // pixels x+3 .. x+6
-    const uint32_t W = __byte_perm(L, C, 0x4321);  // pixels x-3 .. x
-    const uint32_t dn = __vabsdiffu4(N, C), ds = __vabsdiffu4(S, C);
-    const uint32_t de = __vabsdiffu4(E, C), dw = __vabsdiffu4(W, C);
-    // Byte-wise d > t without carries between bytes: with k7 = 127 - t
-    // (t < 128), (d & 0x7F) + k7 carries into bit 7 iff (d & 0x7F) > t, and
-    // a set bit 7 of d alone means d >= 128 > t; with k7 = 255 - t
-    // (t >= 128) the carry means (d & 0x7F) > t - 128, which counts only
-    // together with bit 7 of d.
-    constexpr uint32_t M7 = 0x7F7F7F7Fu;
-    uint32_t fn = (dn & M7) + k7, fs = (ds & M7) + k7, fe = (de & M7) + k7, fw = (dw & M7) + k7;
-    if (HIGH_T) {
-        fn &= dn; fs &= ds; fe &= de; fw &= dw;
-    } else {
-        fn |= dn; fs |= ds; fe |= de; fw |= dw;
-    }
-    uint32_t keep;
-    if (THREE)  // at least 3 of 4 (any 3 of 4 cyclic positions are consecutive)
-        keep = (fn & fe & (fs | fw)) | (fs & fw & (fn | fe));
-    else        // two adjacent: (N|S) & (E|W)
-        keep = (fn | fs) & (fe | fw);
-    return keep & 0x80808080u;
-}
-
-// Byte-wise d > t of coarse4, for one word of differences.
+// Byte-wise |a - b| > t for the 4 pixels of a word, without carries between
+// bytes: with k7 = 127 - t (t < 128), (d & 0x7F) + k7 carries into bit 7 iff
+// (d & 0x7F) > t, and a set bit 7 of d alone means d >= 128 > t; with
+// k7 = 255 - t (t >= 128) the carry means (d & 0x7F) > t - 128, which counts
+// only together with bit 7 of d.  The flags are bit 7 of each byte; the
+// other bits are left over and cleared by the caller.
 template <bool HIGH_T>
-__device__ __forceinline__ uint32_t byte_gt(uint32_t d, uint32_t k7) {
+__device__ __forceinline__ uint32_t gt_flags(uint32_t a, uint32_t b, uint32_t k7) {
+    const uint32_t d = __vabsdiffu4(a, b);
     const uint32_t f = (d & 0x7F7F7F7Fu) + k7;
     return HIGH_T ? (f & d) : (f | d);
-}
-
-// A stronger coarse test on the eight even circle points (0, 2, .., 14: the
-// compass points and the diagonals (+-2, +-2)).  An arc of n >= 9 contiguous
-// points holds at least floor(n/2) >= 4 cyclically consecutive even points,
-// all with |I_x - I_c| > t, so a pixel is kept when four consecutive of the
-// eight differ from the centre by more than t; it never drops a corner.  On
-// the coarser pyramid levels, where a third to a half of the pixels pass
-// coarse4, it halves the pixels that reach the full test.
-//   C, L, R, N, S as in coarse4; UL, UC, UR and DL, DC, DR: the words of C's
-//   column and its neighbours 2 rows up and down.
-template <bool HIGH_T>
-__device__ __forceinline__ uint32_t coarse8(uint32_t C, uint32_t L, uint32_t R, uint32_t N, uint32_t S,
-                                            uint32_t UL, uint32_t UC, uint32_t UR, uint32_t DL, uint32_t DC,
-                                            uint32_t DR, uint32_t k7) {
-    const uint32_t E = __byte_perm(C, R, 0x6543), W = __byte_perm(L, C, 0x4321);
-    // pixels x+2 .. x+5 and x-2 .. x+1 of the rows 2 up and 2 down
-    const uint32_t NE = __byte_perm(UC, UR, 0x5432), NW = __byte_perm(UL, UC, 0x5432);
-    const uint32_t SE = __byte_perm(DC, DR, 0x5432), SW = __byte_perm(DL, DC, 0x5432);
-    const uint32_t fn = byte_gt<HIGH_T>(__vabsdiffu4(N, C), k7), fs = byte_gt<HIGH_T>(__vabsdiffu4(S, C), k7);
-    const uint32_t fe = byte_gt<HIGH_T>(__vabsdiffu4(E, C), k7), fw = byte_gt<HIGH_T>(__vabsdiffu4(W, C), k7);
-    const uint32_t fne = byte_gt<HIGH_T>(__vabsdiffu4(NE, C), k7), fnw = byte_gt<HIGH_T>(__vabsdiffu4(NW, C), k7);
-    const uint32_t fse = byte_gt<HIGH_T>(__vabsdiffu4(SE, C), k7), fsw = byte_gt<HIGH_T>(__vabsdiffu4(SW, C), k7);
-    // the 8 runs of four on the cycle N NE E SE S SW W NW, grouped by their
-    // middle three around a diagonal: run (N..SE) = xne & SE, (NW..E) = NW & xne, ...
-    const uint32_t xne = fn & fne & fe, xse = fe & fse & fs, xsw = fs & fsw & fw, xnw = fw & fnw & fn;
-    return (((xne | xsw) & (fse | fnw)) | ((xse | xnw) & (fne | fsw))) & 0x80808080u;
 }
 
 // ---------------------------------------------------------------------------
@@ -524,75 +478,160 @@ __device__ __forceinline__ Item decode_item(const CallView& cv, const int32_t* t
     return r;
 }
 
+// Transpose of the 32 x 32 bit matrix whose row l is lane l's x: the result
+// in lane b has bit l = bit b of lane l's x.  Five exchange rounds with the
+// lanes l ^ s (s = 16, 8, 4, 2, 1) swap the off-diagonal s x s blocks.
+__device__ __forceinline__ uint32_t transpose_warp_bits(uint32_t x, int lane) {
+    constexpr uint32_t kM[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int sh = 16 >> k;
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, sh);
+        x = (lane & sh) ? ((x & ~kM[k]) | ((y >> sh) & kM[k])) : ((x & kM[k]) | ((y << sh) & ~kM[k]));
+    }
+    return x;
+}
+
 // bits 7, 15, 23, 31 -> bits 28..31: the product's other terms stay below bit 28
 __device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x00204081u) >> 28; }
 
-// Coarse test over this warp's rows, appending kept pixels (score-region index
-// row * 128 + column) to the warp's queue; returns the queue length.
-// Warp w owns row pairs PPW*w .. PPW*w + PPW-1 (lanes 0-15 the even row of a
-// pair, 16-31 the odd one, 8 pixels per lane).  The kept-pixel bits of up to 4
-// row pairs gather in one 32-bit word per lane (bit 8i + j = pair i, pixel j),
-// one warp scan of the popcounts places each lane's run in the queue, and
-// each lane writes its pixels by walking its set bits.  EIGHT selects
-// coarse8 (which also reads the rows 2 up and down, inside the 3-row halo).
+// Coarse test (the CCRF of Algorithm 1) over this warp's score rows,
+// appending the kept pixels (score-region index row * 128 + column) to the
+// warp's queue; returns the queue length.
+//
+// Warp w owns the 2*PPW score rows starting at r0 = 2*PPW*w; lane l owns the
+// 4-pixel word of score columns 4l .. 4l+3 in every one of them, so a row is
+// one conflict-free 128-byte read per warp.  The rule: an arc of n >= 9
+// contiguous points contains floor(n/4) >= 2 cyclically consecutive compass
+// points (0, 4, 8, 12), all darker or all brighter and so all with
+// |I_x - I_c| > t; a pixel is kept when two adjacent compass points (n <= 11)
+// or three of the four (n >= 12) differ from the centre by more than t.  On
+// pyramid levels >= 1 (EIGHT, n <= 11) the stronger rule on the eight even
+// circle points (compass points and the (+-2, +-2) diagonals) applies: an arc
+// of n >= 9 holds floor(n/2) >= 4 cyclically consecutive even points, so a
+// pixel is kept when four consecutive of the eight differ by more than t.
+// Neither rule drops a corner.
+//
+// Each comparison is made once and serves two pixels: rows y and y+3 of a
+// column give the S flag of row y and the N flag of row y+3; columns x and
+// x+3 of a row give the E flag of x and the W flag of x+3 (the W flags of a
+// word come from the E flags of the word to its left, a lane shuffle away);
+// likewise (x, y)-(x+2, y+2) is SE of the first and NW of the second, and
+// (x, y)-(x-2, y+2) is SW of the first and NE of the second.  The shuffles
+// leave the outermost columns of lanes 0 and 31 without the left or right
+// neighbour word; those columns are outside the NMS region for radius 1
+// (lane 0's W flags of columns 0..2) and radius <= 2 (the diagonal flags of
+// columns 0, 1, 126, 127), so a radius of 2 reads the left word for its W
+// flags and radii >= 3 use the compass rule on every level.
+//
+// The kept-pixel bits of a lane gather in 32-bit words (bit 4i + j of word
+// w = row r0 + 8w + i, column 4l + j), which are then spread over the warp
+// by a skewed bit transpose; one warp scan of the popcounts places each
+// lane's run in the queue, and each lane writes its pixels by walking its
+// set bits.
+// vm: bit 7 of byte j set when column 4l + j is inside the columns NMS reads.
 template <bool HIGH_T, bool THREE, int TH, int R, bool EIGHT = false>
 __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* queue, int xw, uint32_t k7,
-                                                  int warp, int lane, int row_lo, int row_hi, uint32_t vm0,
-                                                  uint32_t vm1, uint32_t* status = nullptr) {
+                                                  int warp, int lane, int row_lo, int row_hi, uint32_t vm,
+                                                  uint32_t* status = nullptr) {
     using G = TileGeom<TH, R>;
-    constexpr int RW = G::BW / 4;
-    constexpr int NW = (G::PPW + 3) / 4;  // mask words per lane
-    const int half = lane >> 4, g = lane & 15;
+    constexpr int RW = G::BW / 4;      // words per box row
+    constexpr int RPW = 2 * G::PPW;    // score rows per warp
+    constexpr int NW = (4 * RPW + 31) / 32;  // mask words per lane
+    static_assert(!EIGHT || R <= 2, "the diagonal flags of the edge lanes cover NMS radii <= 2");
+    constexpr uint32_t kFull = 0xFFFFFFFFu;
+    const int r0 = RPW * warp;
+    // this lane's word in box row r0 (score row r is box row r + 3)
+    const uint32_t* col = reinterpret_cast<const uint32_t*>(img) + r0 * RW + xw + lane;
     uint32_t m[NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) m[w] = 0u;
+    // One pass down the rows: step jj reads box row r0 + jj (C[jj]), forms
+    // the comparisons that row completes, and emits score row i = jj - 6,
+    // whose flags are then all known:
+    //   Dv[j]: box rows j and j + 3 (S flags of box row j, N flags of j + 3);
+    //   D1[j] / D2[j]: box row j against the pixels 2 right / 2 left of row
+    //   j + 2 (SE / SW flags of row j, NW / NE flags of row j + 2).
+    uint32_t C[RPW + 6], Dv[RPW + 3], D1[RPW + 3], D2[RPW + 3];
 #pragma unroll
-    for (int i = 0; i < G::PPW; ++i) {
-        const int p = G::PPW * warp + i;
-        if (2 * p + 1 < row_lo || 2 * p >= row_hi) continue;  // uniform: no testable row
-        const int r = 2 * p + half;
-        if (r >= row_lo && r < row_hi) {
-            const uint32_t* w = reinterpret_cast<const uint32_t*>(img + (3 + r) * G::BW) + xw + 2 * g;
-            const uint32_t L = w[-1], C0 = w[0], C1 = w[1], Rt = w[2];
-            uint32_t k0, k1;
-            if (EIGHT) {
-                const uint32_t* u = w - 2 * RW;
-                const uint32_t* d = w + 2 * RW;
-                const uint32_t u0 = u[-1], u1 = u[0], u2 = u[1], u3 = u[2];
-                const uint32_t d0 = d[-1], d1 = d[0], d2 = d[1], d3 = d[2];
-                k0 = coarse8<HIGH_T>(C0, L, C1, w[-3 * RW], w[3 * RW], u0, u1, u2, d0, d1, d2, k7) & vm0;
-                k1 = coarse8<HIGH_T>(C1, C0, Rt, w[1 - 3 * RW], w[1 + 3 * RW], u1, u2, u3, d1, d2, d3, k7) & vm1;
-            } else {
-                k0 = coarse4<HIGH_T, THREE>(C0, L, C1, w[-3 * RW], w[3 * RW], k7) & vm0;
-                k1 = coarse4<HIGH_T, THREE>(C1, C0, Rt, w[1 - 3 * RW], w[1 + 3 * RW], k7) & vm1;
-            }
-            m[i >> 2] |= (nibble(k0) | (nibble(k1) << 4)) << (8 * (i & 3));
+    for (int jj = 0; jj < RPW + 6; ++jj) {
+        C[jj] = col[jj * RW];
+        if (jj >= 3) Dv[jj - 3] = gt_flags<HIGH_T>(C[jj - 3], C[jj], k7);
+        if (EIGHT && jj >= 3 && jj - 2 < RPW + 3) {
+            const int j = jj - 2;
+            const uint32_t r2 = col[jj * RW + 1];
+            const uint32_t l2 = __shfl_up_sync(kFull, C[jj], 1);
+            D1[j] = gt_flags<HIGH_T>(C[j], __byte_perm(C[jj], r2, 0x5432), k7);
+            D2[j] = gt_flags<HIGH_T>(C[j], __byte_perm(l2, C[jj], 0x5432), k7);
         }
+        if (jj < 6) continue;
+        const int i = jj - 6;  // score row r0 + i is box row r0 + j
+        const int j = i + 3;
+        const uint32_t c = C[j];
+        const uint32_t rw = col[j * RW + 1];
+        // E flags of this word; W flags from the E flags of the word to the left
+        const uint32_t fe = gt_flags<HIGH_T>(c, __byte_perm(c, rw, 0x6543), k7);
+        uint32_t el;
+        if (R == 1) {
+            el = __shfl_up_sync(kFull, fe, 1);
+        } else {
+            const uint32_t lw = col[j * RW - 1];
+            el = gt_flags<HIGH_T>(lw, __byte_perm(lw, c, 0x6543), k7);
+        }
+        const uint32_t fw = __byte_perm(el, fe, 0x4321);
+        const uint32_t fn = Dv[i], fs = Dv[j];
+        uint32_t keep;
+        if (EIGHT) {
+            const uint32_t fse = D1[j], fsw = D2[j];
+            const uint32_t fnw = __byte_perm(__shfl_up_sync(kFull, D1[j - 2], 1), D1[j - 2], 0x5432);
+            const uint32_t fne = __byte_perm(D2[j - 2], __shfl_down_sync(kFull, D2[j - 2], 1), 0x5432);
+            // the 8 runs of four on the cycle N NE E SE S SW W NW, grouped by
+            // their middle three around a diagonal
+            const uint32_t xne = fn & fne & fe, xse = fe & fse & fs, xsw = fs & fsw & fw, xnw = fw & fnw & fn;
+            keep = ((xne | xsw) & (fse | fnw)) | ((xse | xnw) & (fne | fsw));
+        } else if (THREE) {  // at least 3 of 4 (any 3 of 4 cyclic positions are consecutive)
+            keep = (fn & fe & (fs | fw)) | (fs & fw & (fn | fe));
+        } else {             // two adjacent: (N|S) & (E|W)
+            keep = (fn | fs) & (fe | fw);
+        }
+        const int r = r0 + i;
+        keep &= (r >= row_lo && r < row_hi) ? vm : 0u;
+        m[i / 8] |= nibble(keep) << (4 * (i % 8));
     }
+    // Spread each lane's candidates over the warp before the walk: the
+    // candidates of a lane lie in one 4-pixel column, and an edge along a
+    // column would leave one lane walking many bits while the others wait.
+    // Lane l's word, rotated left by l, is transposed as a 32 x 32 bit
+    // matrix (rows = lanes): lane b then holds bit (b - l) mod 32 of lane l's
+    // word in its bit l, i.e. one skewed diagonal of the warp's pixels.
+#pragma unroll
+    for (int w = 0; w < NW; ++w) m[w] = transpose_warp_bits(__funnelshift_l(m[w], m[w], lane), lane);
     int cnt = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) cnt += __popc(m[w]);
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        const int y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += y;
     }
     int pos = incl - cnt;
-    // pixel of bit b of word w: pair 4w + (b >> 3), column 8g + (b & 7)
-    const int base = (2 * G::PPW * warp + half) * G::SW + 8 * g;
+    // bit l of word w: lane l's bit q = (lane - l) mod 32 of its word w, the
+    // pixel of row r0 + 8w + (q >> 2), column 4l + (q & 3)
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         uint32_t mw = m[w];
+        const int base = (r0 + 8 * w) * G::SW;
         while (mw) {
-            const int b = 31 - __clz(mw);
-            mw ^= 1u << b;
-            const int e = base + (4 * w + (b >> 3)) * (2 * G::SW) + (b & 7);
+            const int l = 31 - __clz(mw);
+            mw ^= 1u << l;
+            const int q = (lane - l) & 31;
+            const int e = base + (q >> 2) * G::SW + 4 * l + (q & 3);
             if (vio_guard(pos < G::QCAP && e < G::SR * G::SW, status)) queue[pos] = (uint16_t)e;
             ++pos;
         }
     }
-    return __shfl_sync(0xFFFFFFFFu, incl, 31);
+    return __shfl_sync(kFull, incl, 31);
 }
 
 // Consumer warps synchronise with their neighbours only.  Warp w owns score
@@ -754,24 +793,23 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             // score row r is level y = y0 - R + r; score column c is level x = x0 - 4 + c
             const int row_lo = max(0, 3 - y0 + R), row_hi = min(G::SR, Hk - 3 - y0 + R);
             // NMS needs scores of score columns 4-R .. 123+R (x0-R .. x0+119+R) only
-            const int sx = 8 * (lane & 15);           // score column of this lane's first pixel
+            const int sx = 4 * lane;                  // score column of this lane's first pixel
             const int xlo = max(4 - R, 7 - x0), xhi = min(124 + R, Wk + 1 - x0);  // kept score columns [xlo, xhi)
-            uint32_t vm0 = 0, vm1 = 0;
+            uint32_t vm = 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                vm0 |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
-                vm1 |= (sx + 4 + j >= xlo && sx + 4 + j < xhi) ? 0x80u << (8 * j) : 0u;
-            }
+            for (int j = 0; j < 4; ++j) vm |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
             const int xw = xoff / 4;
-            if (!three && k > 0) {  // levels >= 1: the 8-point test (n <= 11; n >= 12 keeps 3 of 4)
-                total = high_t ? coarse_and_compact<true, false, TH, R, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status)
-                               : coarse_and_compact<false, false, TH, R, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status);
+            // levels >= 1: the 8-point test (n <= 11 and NMS radius <= 2; n >= 12 keeps 3 of 4)
+            constexpr bool kEight = R <= 2;
+            if (!three && k > 0) {
+                total = high_t ? coarse_and_compact<true, false, TH, R, kEight>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
+                               : coarse_and_compact<false, false, TH, R, kEight>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
             } else if (high_t) {
-                total = three ? coarse_and_compact<true, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status)
-                              : coarse_and_compact<true, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status);
+                total = three ? coarse_and_compact<true, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
+                              : coarse_and_compact<true, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
             } else {
-                total = three ? coarse_and_compact<false, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status)
-                              : coarse_and_compact<false, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm0, vm1, status);
+                total = three ? coarse_and_compact<false, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
+                              : coarse_and_compact<false, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
             }
         }
         __syncwarp();

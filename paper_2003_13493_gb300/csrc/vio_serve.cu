@@ -50,7 +50,8 @@ struct Result {
 struct Lane {
     vio_ctx* ctx = nullptr;
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done = nullptr;       // after the batch's last operation (timed)
+    cudaEvent_t start = nullptr;      // before its first operation (timed)
     vio_feature* d_cells = nullptr;   // cells of all frames, then int32 counts
     size_t cells_cap = 0;
     uint8_t* h_cells = nullptr;       // pinned copy of d_cells
@@ -75,6 +76,11 @@ struct vio_server_state {
     std::vector<uint64_t> latencies;  // completed requests, ns
     uint64_t next_ticket = 1;
     uint64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched_frames = 0;
+    uint64_t max_batch_frames = 0, max_lanes_in_flight = 0, overlapped_batches = 0;
+    // device-time intervals (ms after t0_ev) of the last retired batch of
+    // each lane, for the overlap count
+    cudaEvent_t t0_ev = nullptr;
+    std::vector<float> last_begin, last_end;
     uint64_t t_first = 0, t_last = 0;
     size_t bytes_in_flight = 0;
     std::atomic<bool> stop{false};
@@ -140,6 +146,7 @@ vio_status launch_lane(vio_server_state* S, Lane& L) {
     const size_t cell_bytes = cell_need * sizeof(vio_feature) + sizeof(int32_t) * n;
     vio_status st;
     if (cell_bytes > L.cells_cap || cell_bytes > L.h_cap) cudaStreamSynchronize(L.stream);
+    if (cudaEventRecord(L.start, L.stream) != cudaSuccess) return VIO_ERR_CUDA;
     if ((st = grow_dev((void**)&L.d_cells, &L.cells_cap, cell_bytes)) != VIO_OK) return st;
     if ((st = grow_host(&L.h_cells, &L.h_cap, cell_bytes)) != VIO_OK) return st;
     std::vector<const uint8_t*> frames(n);
@@ -169,9 +176,32 @@ vio_status launch_lane(vio_server_state* S, Lane& L) {
     return VIO_OK;
 }
 
-void finish_lane(vio_server_state* S, Lane& L) {
+void finish_lane(vio_server_state* S, Lane& L, int lane_index) {
     const int n = (int)L.batch.size();
     const uint64_t t = now_ns();
+    // this batch's device-time interval against the other lanes' latest ones
+    // (a lane's batches run one after another, so a batch of lane j that
+    // overlaps this one is j's latest retired batch or one still running)
+    float b = 0.f, e = 0.f;
+    const bool timed = cudaEventElapsedTime(&b, S->t0_ev, L.start) == cudaSuccess &&
+                       cudaEventElapsedTime(&e, S->t0_ev, L.done) == cudaSuccess;
+    bool overlapped = false;
+    if (timed) {
+        for (int j = 0; j < (int)S->lanes.size(); ++j) {
+            if (j == lane_index) continue;
+            if (S->last_end[j] > S->last_begin[j] && S->last_begin[j] < e && b < S->last_end[j]) overlapped = true;
+            const Lane& O = S->lanes[j];
+            float ob = 0.f;
+            // a batch still in flight on lane j that began before this one ended
+            if (O.busy && cudaEventQuery(O.start) == cudaSuccess &&
+                cudaEventElapsedTime(&ob, S->t0_ev, O.start) == cudaSuccess && ob < e)
+                overlapped = true;
+        }
+        S->last_begin[lane_index] = b;
+        S->last_end[lane_index] = e;
+    } else {
+        cudaGetLastError();
+    }
     // the batch is complete; a device-side status of the lane stops serving
     const vio_status dst = vio_sync(L.ctx, reinterpret_cast<vio_stream>(L.stream));
     if (dst != VIO_OK) {
@@ -198,6 +228,7 @@ void finish_lane(vio_server_state* S, Lane& L) {
         }
     }
     S->completed += n;
+    S->overlapped_batches += overlapped ? 1 : 0;
     S->t_last = t;
     S->bytes_in_flight -= L.bytes;
     L.bytes = 0;
@@ -213,9 +244,10 @@ void worker_main(vio_server_state* S) {
     while (true) {
         bool progressed = false;
         // retire finished lanes
-        for (auto& L : S->lanes) {
+        for (int li = 0; li < (int)S->lanes.size(); ++li) {
+            Lane& L = S->lanes[li];
             if (L.busy && cudaEventQuery(L.done) == cudaSuccess) {
-                finish_lane(S, L);
+                finish_lane(S, L, li);
                 progressed = true;
             }
         }
@@ -242,6 +274,10 @@ void worker_main(vio_server_state* S) {
                 if (L.batch.empty()) break;
                 S->batches += 1;
                 S->batched_frames += L.batch.size();
+                S->max_batch_frames = std::max<uint64_t>(S->max_batch_frames, L.batch.size());
+                uint64_t in_flight = 1;
+                for (const auto& O : S->lanes) in_flight += (&O != &L && O.busy) ? 1 : 0;
+                S->max_lanes_in_flight = std::max(S->max_lanes_in_flight, in_flight);
             }
             L.busy = true;
             const vio_status st = launch_lane(S, L);
@@ -281,9 +317,11 @@ void destroy_state(vio_server_state* S) {
         if (L.ctx) vio_destroy(L.ctx);
         if (L.stream) cudaStreamDestroy(L.stream);
         if (L.done) cudaEventDestroy(L.done);
+        if (L.start) cudaEventDestroy(L.start);
         cudaFree(L.d_cells);
         if (L.h_cells) cudaFreeHost(L.h_cells);
     }
+    if (S->t0_ev) cudaEventDestroy(S->t0_ev);
     delete S;
 }
 
@@ -335,10 +373,18 @@ vio_status vio_serve_start(vio_ctx* ctx, const vio_serve_config* cfg) {
             return st;
         }
         if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreate(&L.done) != cudaSuccess || cudaEventCreate(&L.start) != cudaSuccess) {
             destroy_state(S);
             return VIO_ERR_CUDA;
         }
+    }
+    // the origin of the lanes' device-time intervals
+    S->last_begin.assign(cfg->lanes, 0.f);
+    S->last_end.assign(cfg->lanes, 0.f);
+    if (cudaEventCreate(&S->t0_ev) != cudaSuccess || cudaEventRecord(S->t0_ev, S->lanes[0].stream) != cudaSuccess ||
+        cudaEventSynchronize(S->t0_ev) != cudaSuccess) {
+        destroy_state(S);
+        return VIO_ERR_CUDA;
     }
     {
         std::lock_guard<std::mutex> g(g_srv_mu);
@@ -435,6 +481,9 @@ vio_status vio_serve_stats(vio_ctx* ctx, vio_serve_stats_t* out) {
     }
     if (S->completed && S->t_last > S->t_first)
         out->frames_per_s = (double)S->completed / ((double)(S->t_last - S->t_first) * 1e-9);
+    out->max_batch_frames = S->max_batch_frames;
+    out->max_lanes_in_flight = S->max_lanes_in_flight;
+    out->overlapped_batches = S->overlapped_batches;
     return VIO_OK;
 }
 

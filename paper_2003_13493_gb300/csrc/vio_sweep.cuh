@@ -1,9 +1,14 @@
 // Fused threshold / arc-length sweep: up to 8 detector settings (threshold,
 // arc length) over the same frames in one pass.  Each tile is loaded once,
 // the coarse test runs once at the lowest threshold (its candidates are a
-// superset of every setting's), the 16 circle values of a candidate are read
-// once, Eq. 1's labels are formed once per distinct threshold, and the arc
-// test, NMS and cell maximum run per setting on a per-pixel bit mask of the
+// superset of every setting's), and the 16 circle values of a candidate are
+// read once.  Instead of forming Eq. 1's labels per threshold, the full test
+// finds, once per distinct arc length n, the largest threshold at which the
+// candidate is a corner: the segment test holds at t exactly when some n
+// cyclically consecutive signed differences (v - c for a brighter arc, c - v
+// for a darker one) all exceed t, i.e. when the largest minimum over all
+// windows of n points exceeds t.  A setting (t, n) then costs one compare.
+// NMS and the cell maximum run per setting on a per-pixel bit mask of the
 // settings in which the pixel is a corner.  SAD-B is the score: it does not
 // depend on the setting, so one 16-bit score tile serves all of them.
 #pragma once
@@ -18,8 +23,8 @@ constexpr int kMaxSweep = 8;
 // Sweep section of a call block (the detector sections come first).
 struct SweepInfo {
     int32_t n_set;                 // settings in this launch, 1..kMaxSweep
-    int32_t thresh[kMaxSweep];     // non-decreasing
-    int32_t arc[kMaxSweep];
+    int32_t thresh[kMaxSweep];
+    int32_t arc[kMaxSweep];        // non-decreasing: settings of one arc length are adjacent
     int32_t pad;
     int64_t set_stride;            // keys of setting s: FrameDesc::keys + s * set_stride
     int4* const* outs;             // [n_set * n_frames] output records, setting-major
@@ -33,17 +38,56 @@ struct SweepGeom : TileGeom<TH, 1> {
     static constexpr int SMEM = MK_OFF + B::SR * B::SW + 128;
 };
 
-// Eq. 1 labels of the 16 circle points at threshold t: bright mask in bits
-// 0..15, dark mask in bits 16..31 (the biased 16-bit lane IMAD of eval_corner).
-__device__ __forceinline__ uint32_t sweep_labels(const uint32_t (&v)[16], uint32_t c, uint32_t t) {
-    const uint32_t K = ((0x7FFFu - c - t) & 0xFFFFu) | ((0x7FFFu + c - t) << 16);
-    uint32_t a[4] = {0u, 0u, 0u, 0u};
+// Window minima for the sweep's full test.  D[i] holds point i's biased
+// differences, v - c + 256 in the low 16-bit lane (brighter) and c - v + 256
+// in the high lane (darker), both in 1..511 so no lane borrows; W8[i] is the
+// lane-wise minimum over points i .. i+7 (cyclic), from minima of three.
+// p: the candidate in a tile of row pitch PITCH bytes.
+template <int PITCH>
+__device__ __forceinline__ void sweep_windows8(const uint8_t* __restrict__ p, uint32_t (&W8)[16]) {
+    const uint32_t c = p[0];
+    const uint32_t K = (256u - c) | ((256u + c) << 16);
+    uint32_t D[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const uint32_t w = K + v[i] * 0xFFFF0001u;
-        a[i & 3] = (a[i & 3] >> 4) | (w & 0x80008000u);
+    for (int i = 0; i < 16; ++i) D[i] = K + (uint32_t)p[circ_dy(i) * PITCH + circ_dx(i)] * 0xFFFF0001u;
+    uint32_t W3[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) W3[i] = __vimin3_u16x2(D[i], D[(i + 1) & 15], D[(i + 2) & 15]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) W8[i] = __vimin3_u16x2(W3[i], W3[(i + 3) & 15], W3[(i + 5) & 15]);
+}
+
+// Largest minimum over the 16 windows of 8 + R points (both polarities),
+// still biased by 256: the candidate is a corner at threshold t for arc
+// length 8 + R exactly when the result is >= t + 257.  A window of 8 + R
+// points is two overlapping windows of 8, R apart.
+template <int R>
+__device__ __forceinline__ uint32_t sweep_best(const uint32_t (&W8)[16]) {
+    uint32_t m[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) m[i] = min16x2(W8[i], W8[(i + R) & 15]);
+    uint32_t b = __vimax3_u16x2(m[0], m[1], m[2]);
+    b = __vimax3_u16x2(b, m[3], m[4]);
+    b = __vimax3_u16x2(b, m[5], m[6]);
+    b = __vimax3_u16x2(b, m[7], m[8]);
+    b = __vimax3_u16x2(b, m[9], m[10]);
+    b = __vimax3_u16x2(b, m[11], m[12]);
+    b = __vimax3_u16x2(b, m[13], m[14]);
+    b = __vimax3_u16x2(b, m[15], m[15]);
+    return max(b & 0xFFFFu, b >> 16);
+}
+
+__device__ __forceinline__ uint32_t sweep_best_for_arc(const uint32_t (&W8)[16], int n) {
+    switch (n) {  // uniform over the launch
+        case 9: return sweep_best<1>(W8);
+        case 10: return sweep_best<2>(W8);
+        case 11: return sweep_best<3>(W8);
+        case 12: return sweep_best<4>(W8);
+        case 13: return sweep_best<5>(W8);
+        case 14: return sweep_best<6>(W8);
+        case 15: return sweep_best<7>(W8);
+        default: return sweep_best<8>(W8);
     }
-    return (a[0] >> 3) | (a[1] >> 2) | (a[2] >> 1) | a[3];
 }
 
 template <int TH>
@@ -109,7 +153,8 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
     const uint32_t lt_mask = (1u << lane) - 1u;
     // the coarse test at the lowest threshold with the two-adjacent rule
     // keeps every pixel any setting can accept
-    const int tmin = set_t[0];
+    int tmin = set_t[0];
+    for (int s = 1; s < n_set; ++s) tmin = min(tmin, set_t[s]);
     const bool high_t = tmin >= 128;
     const uint32_t k7 = (uint32_t)((high_t ? 255 : 127) - tmin) * 0x01010101u;
     const int64_t stride = sw->set_stride;
@@ -130,26 +175,23 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
         int total;
         {
             const int row_lo = max(0, 4 - y0), row_hi = min(G::SR, Hk - 2 - y0);
-            const int sx = 8 * (lane & 15);
+            const int sx = 4 * lane;
             const int xlo = max(3, 7 - x0), xhi = min(125, Wk + 1 - x0);
-            uint32_t vm0 = 0, vm1 = 0;
+            uint32_t vm = 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                vm0 |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
-                vm1 |= (sx + 4 + j >= xlo && sx + 4 + j < xhi) ? 0x80u << (8 * j) : 0u;
-            }
+            for (int j = 0; j < 4; ++j) vm |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
             const int xw = xoff / 4;
             // levels >= 1: the 8-point test, also a necessary condition for every arc length
             if (k > 0)
                 total = high_t ? coarse_and_compact<true, false, TH, 1, true>(img, queue, xw, k7, warp, lane, row_lo,
-                                                                              row_hi, vm0, vm1, status)
+                                                                              row_hi, vm, status)
                                : coarse_and_compact<false, false, TH, 1, true>(img, queue, xw, k7, warp, lane, row_lo,
-                                                                               row_hi, vm0, vm1, status);
+                                                                               row_hi, vm, status);
             else
                 total = high_t ? coarse_and_compact<true, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo,
-                                                                         row_hi, vm0, vm1, status)
+                                                                         row_hi, vm, status)
                                : coarse_and_compact<false, false, TH, 1>(img, queue, xw, k7, warp, lane, row_lo,
-                                                                          row_hi, vm0, vm1, status);
+                                                                          row_hi, vm, status);
         }
         __syncwarp();
 
@@ -167,21 +209,17 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             int idx = 0;
             if (e < total && vio_guard(e < G::QCAP && queue[e] < G::SR * G::SW, status)) {
                 idx = queue[e];
-                const uint8_t* p = img_base + idx + 16 * (idx >> 7);
-                const uint32_t c = p[0];
-                uint32_t v[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * G::BW + circ_dx(i)];
-                int prev_t = -1;
-                uint32_t acc = 0;
-                for (int s = 0; s < n_set; ++s) {  // uniform
-                    const int ts = set_t[s], ns = set_n[s];
-                    if (ts != prev_t) {
-                        acc = sweep_labels(v, c, (uint32_t)ts);
-                        prev_t = ts;
+                uint32_t W8[16];
+                sweep_windows8<G::BW>(img_base + idx + 16 * (idx >> 7), W8);
+                int prev_n = 0;
+                uint32_t best = 0;
+                for (int s = 0; s < n_set; ++s) {  // uniform; settings of one arc length are adjacent
+                    const int ns = set_n[s];
+                    if (ns != prev_n) {
+                        best = sweep_best_for_arc(W8, ns);
+                        prev_n = ns;
                     }
-                    const uint32_t bm = acc & 0xFFFFu, dm = acc >> 16;
-                    if (arc_starts(__popc(bm) >= ns ? bm : dm, ns)) cmask |= 1u << s;
+                    if (best >= (uint32_t)set_t[s] + 257u) cmask |= 1u << s;
                 }
             }
             const uint32_t cm = __ballot_sync(0xFFFFFFFFu, cmask != 0);

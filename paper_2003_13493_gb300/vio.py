@@ -50,7 +50,8 @@ class ServeStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
                 ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double),
-                ("frames_per_s", ctypes.c_double)]
+                ("frames_per_s", ctypes.c_double), ("max_batch_frames", ctypes.c_uint64),
+                ("max_lanes_in_flight", ctypes.c_uint64), ("overlapped_batches", ctypes.c_uint64)]
 
 
 class TrackParams(ctypes.Structure):

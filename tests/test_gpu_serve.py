@@ -65,6 +65,43 @@ def test_results_same_alone_and_in_the_mix(pool):
     det.close()
 
 
+def test_batches_form_and_lanes_overlap(pool):
+    """A burst of frames submitted faster than one lane detects them: pending
+    frames must be admitted as multi-frame batches into the free lanes, at
+    least two lanes must hold batches at once, and some batches must overlap
+    another lane's on the device timeline (CUDA events around each lane's
+    work); every result still equals the oracle's."""
+    keep, frames = [], []
+    for sid, f in pool:
+        buf = torch.empty(f.shape, dtype=torch.uint8).pin_memory()
+        buf.numpy()[...] = f
+        keep.append(buf)
+        frames.append((sid, buf.numpy()))
+    det = vio.Detector(max_frames=64)
+    det.serve_start(max_batch=8, lanes=3, **PARAMS)
+    order = [(i * 5) % len(frames) for i in range(120)]
+    tickets = [(det.submit(*frames[i]), i) for i in order]
+    det.drain(60000)
+    st = det.serve_stats()
+    want = {}
+    for t, i in tickets:
+        f = frames[i][1]
+        done, cells, cnt = det.poll(t, f.shape[1], f.shape[0])
+        assert done
+        if i not in want:
+            want[i] = oracle.detect(np.ascontiguousarray(f), PARAMS["thresh"], PARAMS["arc_len"],
+                                    PARAMS["cell_size"], PARAMS["levels"])
+        ref, n = want[i]
+        assert np.array_equal(cells, ref) and cnt == n, i
+    assert st["completed"] == len(tickets)
+    assert st["max_batch_frames"] > 1 and st["mean_batch"] > 1.0, st
+    assert st["max_lanes_in_flight"] >= 2, st
+    assert st["overlapped_batches"] >= 1, st
+    assert st["batches"] < len(tickets)
+    det.serve_stop()
+    det.close()
+
+
 def test_queue_full_and_budget(pool):
     det = vio.Detector(max_frames=64)
     # a budget of ~2 large frames: frames are admitted as memory frees up

@@ -59,7 +59,7 @@ def _byte_perm(a, b, sel):
 
 
 def test_coarse_shifts_select_the_circle_columns():
-    """The byte selections of coarse4/coarse8: with C = pixels x..x+3 and
+    """The byte selections of the coarse test: with C = pixels x..x+3 and
     its neighbour words L, R, 0x6543 gives x+3.., 0x4321 gives x-3.., 0x5432
     gives x+2.. from (C, R) and x-2.. from (L, C)."""
     row = list(range(12))  # pixel values = their column; C holds columns 4..7
@@ -73,7 +73,7 @@ def test_coarse_shifts_select_the_circle_columns():
 
 
 def _eight(f):
-    """coarse8's keep formula on the flags of N, NE, E, SE, S, SW, W, NW."""
+    """The 8-point keep formula on the flags of N, NE, E, SE, S, SW, W, NW."""
     fn, fne, fe, fse, fs, fsw, fw, fnw = f
     xne, xse, xsw, xnw = fn & fne & fe, fe & fse & fs, fs & fsw & fw, fw & fnw & fn
     return ((xne | xsw) & (fse | fnw)) | ((xse | xnw) & (fne | fsw))
@@ -92,7 +92,7 @@ def test_eight_point_formula_is_four_consecutive():
 
 def test_eight_point_test_never_drops_a_corner():
     """Every 16-point mask with a cyclic run of n (9..16) has four
-    consecutive even points (0, 2, .., 14) set, so coarse8 keeps it."""
+    consecutive even points (0, 2, .., 14) set, so the 8-point rule keeps it."""
     for n in range(9, 17):
         for m in range(1 << 16):
             if _has_run(m, n):
@@ -102,7 +102,7 @@ def test_eight_point_test_never_drops_a_corner():
 def test_even_circle_points_are_compass_and_diagonals():
     """The Bresenham circle of radius 3 (points numbered clockwise from the
     top, as in FAST) has its even points at the compass points and the four
-    (+-2, +-2) diagonals, in the cyclic order coarse8 assumes."""
+    (+-2, +-2) diagonals, in the cyclic order the 8-point rule assumes."""
     circle = [(0, -3), (1, -3), (2, -2), (3, -1), (3, 0), (3, 1), (2, 2), (1, 3),
               (0, 3), (-1, 3), (-2, 2), (-3, 1), (-3, 0), (-3, -1), (-2, -2), (-1, -3)]
     ring = {(x, y) for x in range(-3, 4) for y in range(-3, 4) if 2.5 <= (x * x + y * y) ** 0.5 < 3.5}
@@ -216,3 +216,200 @@ def test_nibble_to_byte_mask_exact():
     for nib in range(16):
         m = ((nib * 0x00204081) & 0x01010101) * 0xFF
         assert m == sum(0xFF << (8 * i) for i in range(4) if (nib >> i) & 1)
+
+
+# ---- coarse test with shared comparisons, one warp modelled lane by lane -----
+
+def _vabsdiff4(a, b):
+    return sum(abs(((a >> (8 * i)) & 0xFF) - ((b >> (8 * i)) & 0xFF)) << (8 * i) for i in range(4))
+
+
+def _gt_flags(a, b, t):
+    """gt_flags: bit 7 of byte i set iff |a_i - b_i| > t (other bits left over)."""
+    high = t >= 128
+    k7 = ((255 if high else 127) - t) * 0x01010101
+    d = _vabsdiff4(a, b)
+    f = ((d & M7) + k7) & 0xFFFFFFFF
+    return (f & d) if high else (f | d)
+
+
+def _shfl_up(vals):
+    """__shfl_up_sync(.., 1): lane l gets lane l-1's value, lane 0 keeps its own."""
+    return [vals[0]] + vals[:-1]
+
+
+def _shfl_down(vals):
+    return vals[1:] + [vals[-1]]
+
+
+def _coarse_warp(box, xw, t, rows, three, eight, radius):
+    """The kernel's coarse_and_compact flags for one warp: rows score rows
+    starting at r0 = 0 (box rows 3 ..), 32 lanes of 4 pixels each; returns
+    kept[(row, column)] before the column and row masks."""
+    word = lambda row, w: sum(int(box[row, 4 * w + j]) << (8 * j) for j in range(4))
+    C = [[word(j, xw + l) for l in range(32)] for j in range(rows + 6)]
+    Rw = [[word(j, xw + l + 1) for l in range(32)] for j in range(rows + 6)]
+    Lw = [[word(j, xw + l - 1) for l in range(32)] for j in range(rows + 6)]
+    Dv = [[_gt_flags(C[j][l], C[j + 3][l], t) for l in range(32)] for j in range(rows + 3)]
+    D1, D2 = {}, {}
+    for j in range(1, rows + 3):
+        left = _shfl_up(C[j + 2])
+        D1[j] = [_gt_flags(C[j][l], _byte_perm(C[j + 2][l], Rw[j + 2][l], 0x5432), t) for l in range(32)]
+        D2[j] = [_gt_flags(C[j][l], _byte_perm(left[l], C[j + 2][l], 0x5432), t) for l in range(32)]
+    kept = {}
+    for i in range(rows):
+        j = i + 3
+        fe = [_gt_flags(C[j][l], _byte_perm(C[j][l], Rw[j][l], 0x6543), t) for l in range(32)]
+        if radius == 1:
+            el = _shfl_up(fe)
+        else:
+            el = [_gt_flags(Lw[j][l], _byte_perm(Lw[j][l], C[j][l], 0x6543), t) for l in range(32)]
+        nwl = _shfl_up(D1[j - 2]) if eight else None
+        ner = _shfl_down(D2[j - 2]) if eight else None
+        for l in range(32):
+            fw = _byte_perm(el[l], fe[l], 0x4321)
+            fn, fs = Dv[i][l], Dv[j][l]
+            if eight:
+                fse, fsw = D1[j][l], D2[j][l]
+                fnw = _byte_perm(nwl[l], D1[j - 2][l], 0x5432)
+                fne = _byte_perm(D2[j - 2][l], ner[l], 0x5432)
+                keep = _eight([fn, fne, fe[l], fse, fs, fsw, fw, fnw])
+            elif three:
+                keep = (fn & fe[l] & (fs | fw)) | (fs & fw & (fn | fe[l]))
+            else:
+                keep = (fn | fs) & (fe[l] | fw)
+            for b in range(4):
+                kept[(i, 4 * l + b)] = bool((keep >> (8 * b + 7)) & 1)
+    return kept
+
+
+def _coarse_reference(box, xoff, t, rows, three, eight):
+    out = {}
+    for i in range(rows):
+        y = i + 3
+        for col in range(128):
+            x = col + xoff
+            c = int(box[y, x])
+            d = lambda dx, dy: abs(int(box[y + dy, x + dx]) - c) > t
+            fn, fe, fs, fw = d(0, -3), d(3, 0), d(0, 3), d(-3, 0)
+            if eight:
+                f = [fn, d(2, -2), fe, d(2, 2), fs, d(-2, 2), fw, d(-2, -2)]
+                out[(i, col)] = any(all(f[(s + k) % 8] for k in range(4)) for s in range(8))
+            elif three:
+                out[(i, col)] = fn + fe + fs + fw >= 3
+            else:
+                out[(i, col)] = (fn or fs) and (fe or fw)
+    return out
+
+
+def test_shared_comparison_coarse_test_matches_the_rule():
+    """The per-lane coarse test (each comparison made once and shared by two
+    pixels, neighbour words by lane shuffles) keeps exactly the pixels the
+    compass / 8-point rules keep, on every column the NMS reads."""
+    rng = np.random.default_rng(11)
+    rows = 8
+    for trial in range(24):
+        xoff = 4 if trial % 2 == 0 else 12
+        xw = xoff // 4
+        # smooth background plus sharp blocks: every flag combination occurs
+        box = np.clip(rng.normal(128, 25, (rows + 6, 144)), 0, 255).astype(np.int64)
+        for _ in range(12):
+            y, x = rng.integers(0, rows + 6), rng.integers(0, 140)
+            box[y:y + rng.integers(1, 6), x:x + rng.integers(1, 8)] = rng.integers(0, 256)
+        t = [0, 5, 15, 40, 127, 128, 200][trial % 7]
+        three = trial % 5 == 4
+        eight = not three and trial % 3 != 0
+        radius = 1 if trial % 4 < 2 else 2
+        got = _coarse_warp(box, xw, t, rows, three, eight, radius)
+        want = _coarse_reference(box, xoff, t, rows, three, eight)
+        for col in range(4 - radius, 124 + radius):
+            for i in range(rows):
+                assert got[(i, col)] == want[(i, col)], (trial, i, col, t, three, eight, radius)
+
+
+def test_prmt_sign_flags_build_the_masks():
+    """eval_corner's mask assembly: prmt with sign replication of the label
+    words of points i and i + 8, bit i of each byte, a final byte reorder;
+    equals the Eq. 1 masks (bright bits 0..15, dark bits 16..31)."""
+    def prmt(a, b, sel):
+        src = [(a >> (8 * k)) & 0xFF for k in range(4)] + [(b >> (8 * k)) & 0xFF for k in range(4)]
+        out = 0
+        for k in range(4):
+            nib = (sel >> (4 * k)) & 0xF
+            byte = src[nib & 7]
+            if nib & 8:
+                byte = 0xFF if byte & 0x80 else 0
+            out |= byte << (8 * k)
+        return out
+    rng = np.random.default_rng(12)
+    for _ in range(20000):
+        c, t = int(rng.integers(0, 256)), int(rng.integers(0, 256))
+        v = [int(x) if rng.random() < 0.5 else int(np.clip(c + rng.integers(-t - 2, t + 3), 0, 255))
+             for x in rng.integers(0, 256, 16)]
+        K = ((0x7FFF - c - t) & 0xFFFF) | (((0x7FFF + c - t) & 0xFFFF) << 16)
+        w = [(K + x * 0xFFFF0001) & 0xFFFFFFFF for x in v]
+        acc = 0
+        for i in range(8):
+            acc |= prmt(w[i], w[i + 8], 0xFDB9) & (0x01010101 << i)
+        acc = prmt(acc, 0, 0x3120)
+        want = sum(1 << i for i in range(16) if v[i] > c + t) | (sum(1 << i for i in range(16) if v[i] < c - t) << 16)
+        assert acc == want
+
+
+def test_sweep_window_minima_give_the_segment_test():
+    """The sweep's full test: with D_i = (v_i - c + 256) | (c - v_i + 256) << 16,
+    minima of three and of eight points, and windows of n = 8 + R as two
+    windows of 8 that are R apart, the largest window minimum is >= t + 257
+    exactly when the pixel is a corner at threshold t with arc length n."""
+    rng = np.random.default_rng(13)
+    for trial in range(4000):
+        c = int(rng.integers(0, 256))
+        v = [int(x) for x in np.clip(c + rng.integers(-60, 61, 16), 0, 255)]
+        if trial % 2:
+            s0, L, sg = int(rng.integers(0, 16)), int(rng.integers(8, 17)), 1 if rng.random() < 0.5 else -1
+            for j in range(L):
+                v[(s0 + j) % 16] = int(np.clip(c + sg * rng.integers(1, 90), 0, 255))
+        D = [(x - c + 256) | ((c - x + 256) << 16) for x in v]
+        lo = lambda w: w & 0xFFFF
+        hi = lambda w: w >> 16
+        mn = lambda *ws: (min(lo(w) for w in ws)) | (min(hi(w) for w in ws) << 16)
+        W3 = [mn(D[i], D[(i + 1) % 16], D[(i + 2) % 16]) for i in range(16)]
+        W8 = [mn(W3[i], W3[(i + 3) % 16], W3[(i + 5) % 16]) for i in range(16)]
+        for n in range(9, 17):
+            Wn = [mn(W8[i], W8[(i + n - 8) % 16]) for i in range(16)]
+            best = max(max(lo(w), hi(w)) for w in Wn)
+            for t in (0, 5, 10, 20, 40, 100, 255):
+                b = sum(1 << i for i in range(16) if v[i] > c + t)
+                d = sum(1 << i for i in range(16) if v[i] < c - t)
+                assert (best >= t + 257) == (_has_run(b, n) or _has_run(d, n)), (v, c, t, n)
+
+
+def _transpose_warp_bits(xs):
+    """transpose_warp_bits for all 32 lanes: exchange rounds with lane ^ s."""
+    M = [0x0000FFFF, 0x00FF00FF, 0x0F0F0F0F, 0x33333333, 0x55555555]
+    xs = list(xs)
+    for k in range(5):
+        sh = 16 >> k
+        ys = [xs[l ^ sh] for l in range(32)]
+        xs = [((x & ~M[k]) | ((y >> sh) & M[k])) & 0xFFFFFFFF if (l & sh) else
+              ((x & M[k]) | ((y << sh) & ~M[k])) & 0xFFFFFFFF for l, (x, y) in enumerate(zip(xs, ys))]
+    return xs
+
+
+def test_skewed_transpose_spreads_every_bit_once():
+    """Rotating lane l's word left by l and transposing gives lane b the bit
+    (b - l) mod 32 of lane l as its bit l: every candidate is walked once."""
+    rng = np.random.default_rng(14)
+    for _ in range(200):
+        words = [int(x) for x in rng.integers(0, 1 << 32, 32, dtype=np.uint64)]
+        words = [w & int(rng.integers(0, 1 << 32)) for w in words]
+        rot = [((w << l) | (w >> (32 - l))) & 0xFFFFFFFF if l else w for l, w in enumerate(words)]
+        T = _transpose_warp_bits(rot)
+        # plain transpose property
+        plain = _transpose_warp_bits(words)
+        for b in range(32):
+            for l in range(32):
+                assert (plain[b] >> l) & 1 == (words[l] >> b) & 1
+        got = sorted((l, (b - l) & 31) for b in range(32) for l in range(32) if (T[b] >> l) & 1)
+        want = sorted((l, q) for l in range(32) for q in range(32) if (words[l] >> q) & 1)
+        assert got == want
