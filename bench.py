@@ -33,7 +33,7 @@ WORKLOADS = {
     "mixed64": dict(levels=3, thresh=15, arc=9, cell=32,
                     desc="64 frames in one batched launch: 16 each of 640x480, 752x480, 1280x720, "
                          "1920x1080 (seeds 2..65, 40 shapes), 3-level pyramid, FAST-9, thresh 15, "
-                         "3x3 NMS, 32x32 cells, SAD-B"),
+                         "3x3 NMS, 32x32 or 64x64 cells picked by the autotuner, SAD-B"),
     "large4k": dict(levels=4, thresh=10, arc=9, cell=64, sweep=[(t, a) for a in (12, 9) for t in (5, 10, 20, 40)],
                     desc="32 frames of 3840x2160 (seeds 100..131, 400 shapes), 4-level pyramid built once, "
                          "FAST-12 and FAST-9 at thresholds 5, 10, 20, 40 (8 detections per step), 3x3 NMS, "
@@ -273,6 +273,10 @@ def run_ours(args, rank, world, local_rank):
     wl = dict(WORKLOADS[args.workload])
     if args.cell:
         wl["cell"] = args.cell
+    # the mixed batch's cell size (32 or 64) is the autotuner's pick: the timed
+    # calls pass cell_size 0, everything after the warm-up uses the size it chose
+    auto_cell = args.workload == "mixed64" and not args.cell and args.variant < 0
+    call_cell = 0 if auto_cell else wl["cell"]
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     frames_np = make_frames(args.workload)
@@ -293,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
             dev_sets.append([torch.from_numpy(f).to(dev) for f in frames_np])
     sweep = wl.get("sweep")
     npar = len(sweep) if sweep else 1
-    outs = [torch.empty((vio.num_cells(w, h, wl["cell"]), 4), dtype=torch.int32, device=dev)
+    outs = [torch.empty((vio.num_cells(w, h, call_cell or 32), 4), dtype=torch.int32, device=dev)
             for _ in range(npar) for w, h in dims]
     counts = torch.empty(npar * n, dtype=torch.int32, device=dev)
 
@@ -314,12 +318,16 @@ def run_ours(args, rank, world, local_rank):
         if sweep:
             d.detect_sweep_ptrs(fp, dd, n, th, ar, npar, wl["cell"], wl["levels"], optr, cptr, sh)
         else:
-            d.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], wl["cell"], wl["levels"], optr, cptr, sh)
+            d.detect_ptrs(fp, dd, n, wl["thresh"], wl["arc"], call_cell, wl["levels"], optr, cptr, sh)
 
     for i in range(max(3, args.warmup)):
         step(i)
     det.sync(stream)
     tune = det.tuning()
+    tune_full = det.tuning_full()
+    tune_log = det.autotune_log()
+    if auto_cell:
+        wl["cell"] = tune_full["cell_size"]
 
     dist = None
     if world > 1:
@@ -366,13 +374,24 @@ def run_ours(args, rank, world, local_rank):
                    "l2": f"inputs rotate over {sets} device copies of the batch "
                          f"({sets * mpx:.0f} MB > 129 MB L2)",
                    "tile": {"w": tune[0], "h": tune[1], "variant": tune[2],
+                            "rows_per_warp": tune[1] // 8 + (1 if tune[1] % 8 else 0),
+                            "cta_per_sm": tune_full["cta_per_sm"],
                             "picked_by": "autotuner" if args.variant < 0 else "--variant"},
+                   "cell_picked_by": "autotuner (32 or 64)" if auto_cell else ("--cell" if args.cell else "workload"),
                    "parallelism": f"replicas x{world}, no collective"},
         "clocks": clk,
         # per step: the pyramid, then a detect and a decode kernel per launch
         # (a sweep detects up to 8 settings per launch)
         "gpu_launches": args.steps * ((1 if wl["levels"] > 1 else 0) + 2 * ((npar + 7) // 8 if sweep else 1)),
     }
+    if tune_log:
+        res["autotune"] = {"chosen": {k: tune_full[k] for k in ("variant", "tile_h", "cta_per_sm", "cell_size")},
+                           "alternatives": [{k: e[k] for k in ("variant", "tile_h", "cta_per_sm", "cell_size", "ms")}
+                                            for e in tune_log],
+                           "what": "ms per call of every configuration the tuner timed on this batch"}
+    # later legs reuse the tuned configuration instead of tuning again
+    if args.variant < 0:
+        det.set_variant(tune_full["variant"], cta_per_sm=tune_full["cta_per_sm"])
     if sweep:
         res["detections_per_s"] = round(world * n * npar * args.steps / (ms / 1e3), 1)
     if not args.no_extras and not sweep:
@@ -514,7 +533,8 @@ def extras(args, wl, det, dev, stream, sh, frames_np, dims, marshalled, optr, cp
     out = {}
     # roofline of the fused kernel: stage events captured inside the graph
     prof = vio.Detector(device=dev.index, max_frames=max(64, n), profile=True)
-    prof.set_variant(det.tuning()[2])
+    tf = det.tuning_full()
+    prof.set_variant(tf["variant"], cta_per_sm=tf["cta_per_sm"])
     steps = min(args.steps, 200)
     acc = [0.0, 0.0, 0.0]
     sweep = wl.get("sweep")

@@ -139,7 +139,10 @@ size_t vio_num_cells(int w, int h, int cell_size);
  *              would otherwise be 0 for a corner).
  *   arc_len    9..16.
  *   cell_size  a positive multiple of 32 (Section II-C: cell widths are
- *              multiples of the 32-thread warp).
+ *              multiples of the 32-thread warp), or 0: the context picks 32
+ *              or 64 (the autotuner times both when autotune is on, else
+ *              32); out_cells must then hold vio_num_cells(w_i, h_i, 32)
+ *              records per frame, and vio_get_tuning reports the size used.
  *   levels     1..VIO_MAX_LEVELS; the smallest level must be >= 7 x 7.
  *   out_cells  host array of n_frames DEVICE pointers, frame i receiving
  *              vio_num_cells(w_i, h_i, cell_size) vio_feature records in
@@ -229,6 +232,18 @@ vio_status vio_detect_host_async(vio_ctx* ctx, const uint8_t* const* host_frames
  * on), so the figures are device time of each kernel. */
 vio_status vio_stage_ms(vio_ctx* ctx, float* ms3);
 
+/* Copies level `level` (0 .. levels-1) of frame `frame` of the context's
+ * most recent detection call (vio_detect, vio_detect_host[_async],
+ * vio_detect_sweep) into dst: (w >> level) x (h >> level) pixels, rows of
+ * dst_pitch bytes, dst in device or host memory; asynchronous on `stream`
+ * (order it after the detection, e.g. the same stream).  Level 0 is the frame
+ * the detection read (the caller's, or its staged copy); levels >= 1 are the
+ * context's resident pyramid (Section II-B), valid until the context's next
+ * detection call.  A diagnostic of the pyramid stage.  Errors:
+ * VIO_ERR_INVALID_ARG (no detection yet, frame or level out of range, NULL
+ * dst, dst_pitch < the level's width), VIO_ERR_CUDA. */
+vio_status vio_copy_level(vio_ctx* ctx, int frame, int level, uint8_t* dst, int dst_pitch, vio_stream stream);
+
 /* Waits for all work the context enqueued on `stream` and reports any
  * device-side status: VIO_ERR_TIMEOUT when a bounded wait gave up,
  * VIO_ERR_CUDA when the decode found a cell key that does not lie in its
@@ -244,20 +259,35 @@ vio_status vio_sync(vio_ctx* ctx, vio_stream stream);
 vio_status vio_selftest_timeout(vio_ctx* ctx, uint32_t limit_us);
 
 /*
- * Tile configuration of the fused kernel.  tile_w x tile_h level pixels per
- * work item, cta_per_sm resident CTAs per SM for the persistent launch,
- * nms_radius the NMS window the variant was built for.  vio_get_tuning
- * reports the configuration in use; vio_set_tuning pins one
- * (VIO_ERR_INVALID_ARG if it is not one of the built variants or was built
- * for another NMS radius than the context's).  The autotuner only times the
- * variants of the context's radius.
+ * Launch configuration of the fused kernel.  tile_w x tile_h level pixels per
+ * work item (tile_h / 8 score rows per warp: the warp-to-row mapping),
+ * cta_per_sm resident CTAs per SM of the persistent launch (0 = as many as
+ * fit), nms_radius the NMS window the variant was built for, cell_size the
+ * grid cell size of the detection.
+ *
+ * vio_get_tuning reports the configuration of the context's most recent
+ * detection (cta_per_sm resolved to the count launched; cell_size the one
+ * used, also when vio_detect was given cell_size 0).  vio_set_tuning pins a
+ * variant and a CTA count for later calls (NULL unpins; VIO_ERR_INVALID_ARG
+ * if the variant is not one of the built ones, was built for another NMS
+ * radius than the context's, or cta_per_sm is outside 0..4); its tile_w,
+ * tile_h, nms_radius and cell_size fields are ignored.  With autotune on and
+ * nothing pinned, the first vio_detect of a batch shape times every
+ * combination of the radius's variants, 2 to 4 CTAs per SM (as far as they
+ * fit) and, when cell_size is 0, cells of 32 and 64, and keeps the fastest
+ * for that shape; vio_autotune_log returns what that run timed.
  */
 typedef struct {
-    int tile_w, tile_h, cta_per_sm, variant, nms_radius;
+    int tile_w, tile_h, cta_per_sm, variant, nms_radius, cell_size;
 } vio_tuning;
 
 vio_status vio_get_tuning(const vio_ctx* ctx, vio_tuning* out);
 vio_status vio_set_tuning(vio_ctx* ctx, const vio_tuning* t);
+/* The configurations the context's most recent tuning run timed and the
+ * device time of each, in ms per detection call (CUDA events over 5 calls
+ * after 2 untimed ones): copies up to cap entries, returns how many there
+ * are (0 before any tuning run; -1 for a NULL context). */
+int vio_autotune_log(const vio_ctx* ctx, vio_tuning* configs, float* ms, int cap);
 /* Number of built variants and the shape of variant i. */
 int vio_num_variants(void);
 vio_status vio_variant(int i, vio_tuning* out);

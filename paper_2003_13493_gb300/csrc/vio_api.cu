@@ -128,7 +128,7 @@ vio_status encode_map(vio_ctx* ctx, CUtensorMap* out, const void* ptr, int w, in
 }
 
 vio_status check_args(vio_ctx* ctx, const void* frames, const vio_dims* dims, int n, int thresh, int arc,
-                      int cell, int levels, const void* outs) {
+                      int cell, int levels, const void* outs, bool auto_cell = false) {
     if (!ctx) return VIO_ERR_INVALID_ARG;
     if (!frames || !dims || !outs) return fail(ctx, VIO_ERR_INVALID_ARG, "NULL frames, dims or outputs");
     if (n < 1 || n > ctx->cfg.max_frames)
@@ -137,7 +137,8 @@ vio_status check_args(vio_ctx* ctx, const void* frames, const vio_dims* dims, in
     if (ctx->cfg.score == VIO_SCORE_MT && thresh < 1)
         return fail(ctx, VIO_ERR_INVALID_ARG, "the MT score needs thresh >= 1");
     if (arc < 9 || arc > 16) return fail(ctx, VIO_ERR_INVALID_ARG, "arc_len must be in 9..16");
-    if (cell < 32 || cell % 32 != 0) return fail(ctx, VIO_ERR_INVALID_ARG, "cell_size must be a positive multiple of 32");
+    if (!(auto_cell && cell == 0) && (cell < 32 || cell % 32 != 0))
+        return fail(ctx, VIO_ERR_INVALID_ARG, "cell_size must be a positive multiple of 32");
     if (levels < 1 || levels > VIO_MAX_LEVELS) return fail(ctx, VIO_ERR_INVALID_ARG, "levels must be in 1..5");
     for (int i = 0; i < n; ++i) {
         const vio_dims& d = dims[i];
@@ -165,6 +166,26 @@ ShapeKey shape_key(const vio_dims* dims, int n, int cell, int levels) {
 
 constexpr int kSmallDecodeCtas = 8;  // decode grid of a small call
 
+#define VIO_CK_STATUS(call)                \
+    do {                                   \
+        const vio_status s_ = (call);      \
+        if (s_ != VIO_OK) return s_;       \
+    } while (0)
+
+// CTAs of a fused-kernel variant that fit on one SM (sets the variant's
+// dynamic shared-memory attribute the first time).
+vio_status fused_occupancy(vio_ctx* ctx, int variant, int* occ) {
+    if (!ctx->occ_fused[variant]) {
+        const Variant& v = variants()[variant];
+        int o = 0;
+        VIO_CK(cudaFuncSetAttribute(v.fn[ctx->cfg.score], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
+        VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, v.fn[ctx->cfg.score], kThreads, v.smem));
+        ctx->occ_fused[variant] = std::max(1, std::min(o, kMaxCtasPerSm));
+    }
+    *occ = ctx->occ_fused[variant];
+    return VIO_OK;
+}
+
 // Enqueues pyramid -> fused detect -> decode on `s`; launch shapes depend only
 // on the context and on `small` (the kernels read the batch from the call
 // block and stride over whatever grid they get).  A small call (a few frames
@@ -172,7 +193,7 @@ constexpr int kSmallDecodeCtas = 8;  // decode grid of a small call
 // one CTA per SM instead of filling every SM, which saves the start-up of CTAs
 // that would find no work.
 vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s, bool pyramid = true,
-                           bool small = false) {
+                           bool small = false, int ctas = 0) {
     const Variant& v = variants()[variant];
     const int mode = ctx->cfg.score;
     const bool prof = ctx->cfg.profile != 0;
@@ -186,13 +207,10 @@ vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s
         VIO_CK(cudaGetLastError());
     }
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[1], s, rec_flags));
-    if (!ctx->grid_fused[variant]) {
-        int occ = 0;
-        VIO_CK(cudaFuncSetAttribute(v.fn[mode], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
-        VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn[mode], kThreads, v.smem));
-        ctx->grid_fused[variant] = std::max(1, occ) * ctx->sm_count;
-    }
-    const int grid = small ? std::min(ctx->grid_fused[variant], ctx->sm_count) : ctx->grid_fused[variant];
+    int occ = 0;
+    VIO_CK_STATUS(fused_occupancy(ctx, variant, &occ));
+    const int per_sm = ctas > 0 ? std::min(ctas, occ) : occ;
+    const int grid = small ? ctx->sm_count : per_sm * ctx->sm_count;
     v.fn[mode]<<<grid, kThreads, v.smem, s>>>(ctx->d_call, ctx->d_counter, ctx->d_status);
     VIO_CK(cudaGetLastError());
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[2], s, rec_flags));
@@ -204,15 +222,17 @@ vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s
 
 // Graph slot `levels` holds pyramid -> detect -> decode; slot 0 holds
 // detect -> decode alone (the pyramid is already in place).
-vio_status get_graph(vio_ctx* ctx, int variant, int levels, bool pyramid, bool small, cudaGraphExec_t* out) {
-    cudaGraphExec_t& g = ctx->graphs[variant][pyramid ? levels : 0][small ? 1 : 0];
+vio_status get_graph(vio_ctx* ctx, int variant, int levels, bool pyramid, bool small, int ctas,
+                     cudaGraphExec_t* out) {
+    cudaGraphExec_t& g = ctx->graphs[variant][pyramid ? levels : 0][small ? 1 : 0][ctas];
     if (!g) {
-        // the launch attributes are set outside the capture
-        const Variant& v = variants()[variant];
-        VIO_CK(cudaFuncSetAttribute(v.fn[ctx->cfg.score], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
+        // the launch attributes and the occupancy are set up outside the capture
+        int occ = 0;
+        VIO_CK_STATUS(fused_occupancy(ctx, variant, &occ));
+        (void)occ;
         cudaGraph_t graph = nullptr;
         VIO_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        vio_status es = enqueue_kernels(ctx, variant, levels, ctx->capture_stream, pyramid, small);
+        vio_status es = enqueue_kernels(ctx, variant, levels, ctx->capture_stream, pyramid, small, ctas);
         cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (es != VIO_OK) return es;
         VIO_CK(ce);
@@ -353,7 +373,8 @@ vio_status enqueue_sweep(vio_ctx* ctx, int levels, cudaStream_t s, bool pyramid,
 
 vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims,
                   int n, int thresh, int arc, int cell, int levels, int4* const* outs, int32_t* counts,
-                  cudaStream_t s, bool pyramid = true, Upload up = {}, const SweepSpec* sweep = nullptr) {
+                  cudaStream_t s, bool pyramid = true, Upload up = {}, const SweepSpec* sweep = nullptr,
+                  int ctas = 0) {
     const Variant& v = variants()[variant];
     // arena layout
     size_t koff = 0, poff = 0;
@@ -463,6 +484,15 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
                 return st;
         }
     }
+    ctx->last_levels = levels;
+    ctx->last_dims.assign(dims, dims + n);
+    ctx->last_lev.assign(n, {});
+    ctx->last_pitch.assign(n, {});
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < levels; ++k) {
+            ctx->last_lev[i][k] = fds[i].lev[k];
+            ctx->last_pitch[i][k] = fds[i].pitch[k];
+        }
     // tiles: coarsest level first, entry (L-1-k)*n + f
     int acc = 0;
     for (int kk = 0; kk < levels; ++kk) {
@@ -494,6 +524,7 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
 
     const bool small = acc <= ctx->sm_count && blocks[n] <= 2 * ctx->sm_count &&
                        cells[n] <= kSmallDecodeCtas * 256 * 4;
+
     VIO_CK(cudaMemcpyAsync(ctx->d_call, st_base, bytes, cudaMemcpyHostToDevice, s));
     VIO_CK(cudaEventRecord(ctx->ring_ev[slot], s));
     if (sweep) {
@@ -502,17 +533,27 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
             return st;
     } else if (ctx->cfg.use_graphs) {
         cudaGraphExec_t g = nullptr;
-        if ((st = get_graph(ctx, variant, levels, pyramid, small, &g)) != VIO_OK) return st;
+        if ((st = get_graph(ctx, variant, levels, pyramid, small, ctas, &g)) != VIO_OK) return st;
         VIO_CK(cudaGraphLaunch(g, s));
-    } else if ((st = enqueue_kernels(ctx, variant, levels, s, pyramid, small)) != VIO_OK) {
+    } else if ((st = enqueue_kernels(ctx, variant, levels, s, pyramid, small, ctas)) != VIO_OK) {
         return st;
     }
     VIO_CK(cudaEventRecord(ctx->last_ev, s));
     ctx->last_stream = s;
     ctx->have_last = true;
+    int occ = 1;
+    if (!sweep) VIO_CK_STATUS(fused_occupancy(ctx, variant, &occ));
+    ctx->last_ctas = small ? 1 : (ctas > 0 ? std::min(ctas, occ) : occ);
+    ctx->last_cell = cell;
     return VIO_OK;
 }
 
+// Times every combination of the context radius's tile variants, 2 to 4
+// CTAs per SM (as far as they fit) and the candidate cell sizes (32 and 64
+// when the call gave cell 0, else the call's) on the call's own batch: two
+// untimed launches, then 5 timed by CUDA events on the call's stream.  The
+// fastest is kept for the batch shape; every alternative and its time go to
+// the tuning log.
 vio_status autotune(vio_ctx* ctx, const ShapeKey& key, const uint8_t* const* lev0, const int* pitch0,
                     const vio_dims* dims, int n, int thresh, int arc, int cell, int levels, int4* const* outs,
                     int32_t* counts, cudaStream_t s, Upload up = {}) {
@@ -520,36 +561,57 @@ vio_status autotune(vio_ctx* ctx, const ShapeKey& key, const uint8_t* const* lev
     VIO_CK(cudaEventCreate(&e0));
     VIO_CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_v = first_variant(ctx->cfg.nms_radius);
+    vio_ctx::TuneChoice choice{first_variant(ctx->cfg.nms_radius), 0, cell ? cell : 32};
+    ctx->tune_log.clear();
+    ctx->tune_log_ms.clear();
     vio_status st = VIO_OK;
+    const int cells[2] = {cell ? cell : 32, 64};
+    const int n_cells = cell ? 1 : 2;
     for (int vi = 0; vi < (int)variants().size() && st == VIO_OK; ++vi) {
         if (variants()[vi].radius != ctx->cfg.nms_radius) continue;
-        for (int r = 0; r < 2 && st == VIO_OK; ++r)
-            st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s, true, up);
-        if (st != VIO_OK) break;
-        VIO_CK(cudaEventRecord(e0, s));
-        const int reps = 5;
-        for (int r = 0; r < reps && st == VIO_OK; ++r)
-            st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s, true, up);
-        VIO_CK(cudaEventRecord(e1, s));
-        VIO_CK(cudaEventSynchronize(e1));
-        float ms = 0;
-        VIO_CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_v = vi;
+        int occ = 1;
+        if ((st = fused_occupancy(ctx, vi, &occ)) != VIO_OK) break;
+        for (int ctas = std::min(2, occ); ctas <= occ && st == VIO_OK; ++ctas) {
+            for (int ci = 0; ci < n_cells && st == VIO_OK; ++ci) {
+                const int c = cells[ci];
+                for (int r = 0; r < 2 && st == VIO_OK; ++r)
+                    st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, c, levels, outs, counts, s, true, up,
+                                nullptr, ctas);
+                if (st != VIO_OK) break;
+                VIO_CK(cudaEventRecord(e0, s));
+                const int reps = 5;
+                for (int r = 0; r < reps && st == VIO_OK; ++r)
+                    st = launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, c, levels, outs, counts, s, true, up,
+                                nullptr, ctas);
+                VIO_CK(cudaEventRecord(e1, s));
+                VIO_CK(cudaEventSynchronize(e1));
+                float ms = 0;
+                VIO_CK(cudaEventElapsedTime(&ms, e0, e1));
+                ms /= reps;
+                vio_tuning t{variants()[vi].tw, variants()[vi].th, ctas, vi, variants()[vi].radius, c};
+                ctx->tune_log.push_back(t);
+                ctx->tune_log_ms.push_back(ms);
+                if (ms < best) {
+                    best = ms;
+                    choice = {vi, ctas, c};
+                }
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st == VIO_OK) ctx->tuned[key] = best_v;
+    if (st == VIO_OK) ctx->tuned[key] = choice;
     return st;
 }
 
+// Resolves the launch configuration (pinned, tuned or default) and the cell
+// size (cell 0: tuned, else 32) and launches.
 vio_status detect_impl(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitch0, const vio_dims* dims, int n,
                        int thresh, int arc, int cell, int levels, int4* const* outs, int32_t* counts,
                        cudaStream_t s, Upload up = {}) {
     int vi = ctx->pinned_variant;
+    int ctas = ctx->pinned_ctas;
+    int c = cell ? cell : 32;
     if (vi < 0) {
         vi = first_variant(ctx->cfg.nms_radius);
         if (ctx->cfg.autotune) {
@@ -560,11 +622,13 @@ vio_status detect_impl(vio_ctx* ctx, const uint8_t* const* lev0, const int* pitc
                 if (st != VIO_OK) return st;
                 it = ctx->tuned.find(key);
             }
-            vi = it->second;
+            vi = it->second.variant;
+            ctas = it->second.ctas;
+            c = it->second.cell;
         }
     }
     ctx->last_variant = vi;
-    return launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, cell, levels, outs, counts, s, true, up);
+    return launch(ctx, vi, lev0, pitch0, dims, n, thresh, arc, c, levels, outs, counts, s, true, up, nullptr, ctas);
 }
 
 // One warp waits on a barrier that nothing completes; the bounded wait gives
@@ -672,6 +736,20 @@ size_t vio_num_cells(int w, int h, int cell) {
     return (size_t)((w + cell - 1) / cell) * (size_t)((h + cell - 1) / cell);
 }
 
+vio_status vio_copy_level(vio_ctx* ctx, int frame, int level, uint8_t* dst, int dst_pitch, vio_stream stream) {
+    if (!ctx) return VIO_ERR_INVALID_ARG;
+    if (ctx->last_levels < 1 || frame < 0 || frame >= (int)ctx->last_dims.size() || level < 0 ||
+        level >= ctx->last_levels || !dst)
+        return fail(ctx, VIO_ERR_INVALID_ARG, "no such level of the most recent detection");
+    const vio_dims& d = ctx->last_dims[frame];
+    const int w = d.w >> level, h = d.h >> level;
+    if (dst_pitch < w) return fail(ctx, VIO_ERR_INVALID_ARG, "dst_pitch < level width");
+    VIO_CK(cudaSetDevice(ctx->cfg.device));
+    VIO_CK(cudaMemcpy2DAsync(dst, (size_t)dst_pitch, ctx->last_lev[frame][level], (size_t)ctx->last_pitch[frame][level],
+                             (size_t)w, (size_t)h, cudaMemcpyDefault, reinterpret_cast<cudaStream_t>(stream)));
+    return VIO_OK;
+}
+
 int vio_num_variants(void) { return (int)variants().size(); }
 
 vio_status vio_variant(int i, vio_tuning* out) {
@@ -681,7 +759,18 @@ vio_status vio_variant(int i, vio_tuning* out) {
     out->cta_per_sm = 0;
     out->variant = i;
     out->nms_radius = variants()[i].radius;
+    out->cell_size = 0;
     return VIO_OK;
+}
+
+int vio_autotune_log(const vio_ctx* ctx, vio_tuning* configs, float* ms, int cap) {
+    if (!ctx) return -1;
+    const int n = (int)ctx->tune_log.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (configs) configs[i] = ctx->tune_log[i];
+        if (ms) ms[i] = ctx->tune_log_ms[i];
+    }
+    return n;
 }
 
 vio_status vio_create(vio_ctx** out, const vio_config* cfg_in) {
@@ -775,7 +864,7 @@ vio_status vio_detect(vio_ctx* ctx, const uint8_t* const* frames, const vio_dims
                       int arc, int cell, int levels, vio_feature* const* out_cells, int32_t* out_counts,
                       vio_stream stream) {
     NvtxRange nvtx("vio_detect");
-    vio_status st = check_args(ctx, frames, dims, n, thresh, arc, cell, levels, out_cells);
+    vio_status st = check_args(ctx, frames, dims, n, thresh, arc, cell, levels, out_cells, true);
     if (st != VIO_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     VIO_CK(cudaSetDevice(ctx->cfg.device));
@@ -860,7 +949,7 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
                                levels, outs0.data(), out_counts, s)) != VIO_OK)
                 return st;
         }
-        vi = ctx->tuned[key];
+        vi = ctx->tuned[key].variant;
     }
     ctx->last_variant = vi;
     if (ctx->cfg.score == VIO_SCORE_SAD_B && ctx->cfg.nms_radius == 1 && n_params > 1) {
@@ -1039,6 +1128,8 @@ vio_status vio_get_tuning(const vio_ctx* ctx, vio_tuning* out) {
     if (!ctx || !out) return VIO_ERR_INVALID_ARG;
     const int vi = ctx->pinned_variant >= 0 ? ctx->pinned_variant : ctx->last_variant;
     vio_variant(vi, out);
+    out->cta_per_sm = ctx->last_ctas;
+    out->cell_size = ctx->last_cell;
     return VIO_OK;
 }
 
@@ -1046,13 +1137,17 @@ vio_status vio_set_tuning(vio_ctx* ctx, const vio_tuning* t) {
     if (!ctx) return VIO_ERR_INVALID_ARG;
     if (!t) {
         ctx->pinned_variant = -1;
+        ctx->pinned_ctas = 0;
         return VIO_OK;
     }
     if (t->variant < 0 || t->variant >= (int)variants().size())
         return fail(ctx, VIO_ERR_INVALID_ARG, "unknown variant");
     if (variants()[t->variant].radius != ctx->cfg.nms_radius)
         return fail(ctx, VIO_ERR_INVALID_ARG, "variant was built for another NMS radius");
+    if (t->cta_per_sm < 0 || t->cta_per_sm > kMaxCtasPerSm)
+        return fail(ctx, VIO_ERR_INVALID_ARG, "cta_per_sm must be in 0..4");
     ctx->pinned_variant = t->variant;
+    ctx->pinned_ctas = t->cta_per_sm;
     return VIO_OK;
 }
 

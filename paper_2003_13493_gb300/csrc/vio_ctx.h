@@ -6,6 +6,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <array>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -16,6 +17,8 @@
 namespace vio {
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+constexpr int kMaxCtasPerSm = 4;  // the detect kernels' launch bounds
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -128,15 +131,29 @@ struct vio_ctx {
     cudaStream_t last_stream = nullptr;
     bool have_last = false;
 
-    // one graph per (variant, levels, launch shape): every batch shape
-    // replays it; shape 1 is the small-call shape (one CTA per SM at most)
-    cudaGraphExec_t graphs[8][vio::kMaxLevels + 1][2] = {};
-    int grid_fused[8] = {};
+    // one graph per (variant, levels, launch shape, CTAs per SM): every batch
+    // shape replays it; shape 1 is the small-call shape (one CTA per SM at
+    // most); CTAs per SM 0 = as many as fit
+    cudaGraphExec_t graphs[8][vio::kMaxLevels + 1][2][vio::kMaxCtasPerSm + 1] = {};
+    int occ_fused[8] = {};                 // CTAs per SM that fit, per variant
     int grid_sweep = 0;
-    std::unordered_map<ShapeKey, int, ShapeHash> tuned;  // batch shape -> variant
+    struct TuneChoice {
+        int variant, ctas, cell;
+    };
+    std::unordered_map<ShapeKey, TuneChoice, ShapeHash> tuned;  // batch shape -> choice
+    std::vector<vio_tuning> tune_log;      // the alternatives the last tuning run timed
+    std::vector<float> tune_log_ms;
     std::unordered_map<MapKey, CUtensorMap, MapHash> map_cache;
     int pinned_variant = -1;
+    int pinned_ctas = 0;
     int last_variant = 0;
+    int last_ctas = 0;                     // CTAs per SM of the last launch (resolved)
+    int last_cell = 0;                     // cell size of the last detection
+    // levels of the most recent detection call, for vio_copy_level
+    std::vector<std::array<const uint8_t*, vio::kMaxLevels>> last_lev;
+    std::vector<std::array<int, vio::kMaxLevels>> last_pitch;
+    std::vector<vio_dims> last_dims;
+    int last_levels = 0;
     vio::TrackState track;
     vio::HostSlot hslots[vio::kHostSlots];
     int hslot_pos = 0;
@@ -144,11 +161,12 @@ struct vio_ctx {
     void drop_graphs() {
         for (auto& row : graphs)
             for (auto& pair : row)
-                for (auto& g : pair)
-                    if (g) {
-                        cudaGraphExecDestroy(g);
-                        g = nullptr;
-                    }
+                for (auto& shape : pair)
+                    for (auto& g : shape)
+                        if (g) {
+                            cudaGraphExecDestroy(g);
+                            g = nullptr;
+                        }
     }
 };
 

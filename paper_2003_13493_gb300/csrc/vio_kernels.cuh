@@ -10,6 +10,7 @@
 namespace vio {
 
 constexpr int kMaxLevels = 5;
+constexpr int kPrefixCache = 1025;  // prefix-table entries a kernel copies to shared memory (1024 frames)
 constexpr uint32_t kStatusTimeout = 1u;  // a bounded wait gave up
 constexpr uint32_t kStatusBadKey = 2u;   // a decoded cell key lies outside its cell
 constexpr uint32_t kStatusBounds = 4u;   // checked build: an index left its buffer
@@ -99,7 +100,8 @@ __device__ __forceinline__ int upper_index(const int32_t* a, int n, int v) {
 // 2x2 mean of level k rounded half up, (a+b+c+d+2)>>2, taken from the
 // rounded level-k values.  Level 0 is read with 16-byte loads; level 1 is
 // computed two pixels per 32-bit word (16-bit lanes) and stored 8 bytes at a
-// time; the coarser levels, a quarter of the work each, are scalar.
+// time; level 2 adds those words of two rows lane-wise and is stored 4 bytes
+// at a time; levels 3 and 4, a sixteenth of the work and less, are scalar.
 // A CTA covers 512 columns x 8B rows; the grid strides over all CTAs of all
 // frames (blocks[] is the per-frame prefix sum).
 // ---------------------------------------------------------------------------
@@ -113,10 +115,18 @@ __global__ void __launch_bounds__(256) pyramid_kernel(const uint8_t* __restrict_
     constexpr int B1 = B / 2;
     const CallView cv(call);
     const int nf = cv.h->n_frames, nb = cv.h->n_pyr_blocks;
+    // the block prefix sums, searched once per block by every thread: in
+    // shared memory when they fit (a search of the global table is a chain of
+    // dependent loads)
+    __shared__ int32_t blocks_sh[kPrefixCache];
+    const int32_t* blocks = nf < kPrefixCache ? blocks_sh : cv.blocks;
+    if (nf < kPrefixCache)
+        for (int i = threadIdx.x; i <= nf; i += blockDim.x) blocks_sh[i] = cv.blocks[i];
+    __syncthreads();
     for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-        const int f = upper_index(cv.blocks, nf, b);
+        const int f = upper_index(blocks, nf, b);
         const FrameDesc& fd = cv.fds[f];
-        const int lb = b - cv.blocks[f];
+        const int lb = b - blocks[f];
         const int tx = (lb % fd.pyr_bx) * 32 + (threadIdx.x & 31);
         const int ty = (lb / fd.pyr_bx) * 8 + (threadIdx.x >> 5);
         const int W = fd.w, H = fd.h;
@@ -168,34 +178,53 @@ __global__ void __launch_bounds__(256) pyramid_kernel(const uint8_t* __restrict_
                 *reinterpret_cast<uint2*>(fd.lev[1] + (size_t)y1 * fd.pitch[1] + x1) = v;
             }
         }
-        if (L > 2) {
-            // level 1 as scalars, then levels 2.. from the rounded values
-            constexpr int N1 = 8;
-            uint32_t v[B1][N1];
+        if constexpr (L > 2) {
+            // level 2, 4 pixels per thread and row: the two level-1 rows of a
+            // pair added lane-wise, then the two lanes of each word
+            constexpr int B2 = B1 / 2;
+            uint32_t p2[B2][4];
 #pragma unroll
-            for (int j = 0; j < B1; ++j)
+            for (int j = 0; j < B2; ++j) {
 #pragma unroll
-                for (int i = 0; i < N1; ++i) v[j][i] = (q[j][i >> 1] >> (16 * (i & 1))) & 0xFFu;
-            int Wk = W1, Hk = H1, rows = B1, cols = N1;
+                for (int w = 0; w < 4; ++w) {
+                    const uint32_t sum = q[2 * j][w] + q[2 * j + 1][w];
+                    p2[j][w] = ((sum & 0xFFFFu) + (sum >> 16) + 2u) >> 2;
+                }
+                const int y2 = ty * B2 + j, x2 = tx * 4;
+                // pixels past W2 land in the row padding (pitch >= W2 rounded to 128)
+                if (y2 < (H >> 2) && x2 < (W >> 2))
+                    *reinterpret_cast<uint32_t*>(fd.lev[2] + (size_t)y2 * fd.pitch[2] + x2) =
+                        p2[j][0] | (p2[j][1] << 8) | (p2[j][2] << 16) | (p2[j][3] << 24);
+            }
+            if constexpr (L > 3) {
+                // levels 3.. as scalars from the rounded level-2 values
+                constexpr int N2 = 4;
+                uint32_t v[B2][N2];
 #pragma unroll
-            for (int k = 2; k < L; ++k) {
-                rows >>= 1;
-                cols >>= 1;
-                Wk >>= 1;
-                Hk >>= 1;
-                uint8_t* dst = fd.lev[k];
-                const int dp = fd.pitch[k];
+                for (int j = 0; j < B2; ++j)
 #pragma unroll
-                for (int j = 0; j < B1; ++j)
+                    for (int i = 0; i < N2; ++i) v[j][i] = p2[j][i];
+                int Wk = W >> 2, Hk = H >> 2, rows = B2, cols = N2;
 #pragma unroll
-                    for (int i = 0; i < N1; ++i)
-                        if (j < rows && i < cols) {
-                            const uint32_t sum = v[2 * j][2 * i] + v[2 * j][2 * i + 1] + v[2 * j + 1][2 * i] +
-                                                 v[2 * j + 1][2 * i + 1] + 2u;
-                            v[j][i] = sum >> 2;
-                            const int xk = tx * cols + i, yk = ty * rows + j;
-                            if (xk < Wk && yk < Hk) dst[(size_t)yk * dp + xk] = (uint8_t)v[j][i];
-                        }
+                for (int k = 3; k < L; ++k) {
+                    rows >>= 1;
+                    cols >>= 1;
+                    Wk >>= 1;
+                    Hk >>= 1;
+                    uint8_t* dst = fd.lev[k];
+                    const int dp = fd.pitch[k];
+#pragma unroll
+                    for (int j = 0; j < B2; ++j)
+#pragma unroll
+                        for (int i = 0; i < N2; ++i)
+                            if (j < rows && i < cols) {
+                                const uint32_t sum = v[2 * j][2 * i] + v[2 * j][2 * i + 1] + v[2 * j + 1][2 * i] +
+                                                     v[2 * j + 1][2 * i + 1] + 2u;
+                                v[j][i] = sum >> 2;
+                                const int xk = tx * cols + i, yk = ty * rows + j;
+                                if (xk < Wk && yk < Hk) dst[(size_t)yk * dp + xk] = (uint8_t)v[j][i];
+                            }
+                }
             }
         }
     }
@@ -329,7 +358,10 @@ __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, i
     uint32_t v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * P + circ_dx(i)];
-    const uint32_t K = ((0x7FFFu - c - (uint32_t)t) & 0xFFFFu) | ((0x7FFFu + c - (uint32_t)t) << 16);
+    // K = (0x7FFF - c - t) | (0x7FFF + c - t) << 16 as one multiply-add: the
+    // low lane never borrows (0x7FFF - t - c > 0) and the high one never
+    // carries out (0x7FFF - t + c < 2^16)
+    const uint32_t K = (0x7FFFu - (uint32_t)t) * 0x00010001u + c * 0xFFFFu;
     uint32_t w[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) w[i] = K + v[i] * 0xFFFF0001u;
@@ -464,6 +496,7 @@ struct ItemInfo {
     uint64_t* keys;
 };
 
+// Item i of the call's tile table: entry j = (L-1-k)*n + f (coarsest level first).
 __device__ __forceinline__ Item decode_item(const CallView& cv, const int32_t* tiles, int it) {
     const int n = cv.h->n_frames, L = cv.h->levels;
     const int j = upper_index(tiles, n * L, it);
@@ -476,20 +509,6 @@ __device__ __forceinline__ Item decode_item(const CallView& cv, const int32_t* t
     r.ty = t / ntx;
     r.tx = t - r.ty * ntx;
     return r;
-}
-
-// Transpose of the 32 x 32 bit matrix whose row l is lane l's x: the result
-// in lane b has bit l = bit b of lane l's x.  Five exchange rounds with the
-// lanes l ^ s (s = 16, 8, 4, 2, 1) swap the off-diagonal s x s blocks.
-__device__ __forceinline__ uint32_t transpose_warp_bits(uint32_t x, int lane) {
-    constexpr uint32_t kM[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int sh = 16 >> k;
-        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, sh);
-        x = (lane & sh) ? ((x & ~kM[k]) | ((y >> sh) & kM[k])) : ((x & kM[k]) | ((y << sh) & ~kM[k]));
-    }
-    return x;
 }
 
 // bits 7, 15, 23, 31 -> bits 28..31: the product's other terms stay below bit 28
@@ -524,11 +543,14 @@ __device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x002
 // columns 0, 1, 126, 127), so a radius of 2 reads the left word for its W
 // flags and radii >= 3 use the compass rule on every level.
 //
-// The kept-pixel bits of a lane gather in 32-bit words (bit 4i + j of word
-// w = row r0 + 8w + i, column 4l + j), which are then spread over the warp
-// by a skewed bit transpose; one warp scan of the popcounts places each
-// lane's run in the queue, and each lane writes its pixels by walking its
-// set bits.
+// The kept-pixel bits of a lane gather in 32-bit words, eight rows per
+// word (bit 8j + i of word w = row r0 + 8w + i, column 4l + j: each row's
+// flags, bit 7 of each byte, enter at the top and move down one bit per
+// row); one warp scan of the popcounts places each lane's run in the queue,
+// and each lane writes its pixels by walking its set bits.  (Spreading the
+// bits over the warp first, by a skewed bit transpose, balances the walk but
+// scatters the queue, and the full test's circle reads then conflict in
+// shared memory: slower.)
 // vm: bit 7 of byte j set when column 4l + j is inside the columns NMS reads.
 template <bool HIGH_T, bool THREE, int TH, int R, bool EIGHT = false>
 __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* queue, int xw, uint32_t k7,
@@ -594,18 +616,20 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
         } else {             // two adjacent: (N|S) & (E|W)
             keep = (fn | fs) & (fe | fw);
         }
-        const int r = r0 + i;
-        keep &= (r >= row_lo && r < row_hi) ? vm : 0u;
-        m[i / 8] |= nibble(keep) << (4 * (i % 8));
+        // row i of word i / 8 lands in bit i % 8 of each byte after the
+        // remaining shifts of that word: bit 8j + (i % 8) = row, column 4l + j
+        m[i / 8] = (m[i / 8] >> 1) | (keep & 0x80808080u);
     }
-    // Spread each lane's candidates over the warp before the walk: the
-    // candidates of a lane lie in one 4-pixel column, and an edge along a
-    // column would leave one lane walking many bits while the others wait.
-    // Lane l's word, rotated left by l, is transposed as a 32 x 32 bit
-    // matrix (rows = lanes): lane b then holds bit (b - l) mod 32 of lane l's
-    // word in its bit l, i.e. one skewed diagonal of the warp's pixels.
+    // a last word of fewer than 8 rows: its first row down to bit 0
+    if (RPW % 8) m[NW - 1] >>= 8 - RPW % 8;
+    // rows outside the testable area and columns outside the NMS region
+    const uint32_t cols = ((vm >> 7) & 0x01010101u) * 0xFFu;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) m[w] = transpose_warp_bits(__funnelshift_l(m[w], m[w], lane), lane);
+    for (int w = 0; w < NW; ++w) {
+        const int lo = min(max(row_lo - r0 - 8 * w, 0), 8), hi = min(max(row_hi - r0 - 8 * w, 0), 8);
+        const uint32_t rows = ((0xFFu << lo) & ~(0xFFu << hi) & 0xFFu) * 0x01010101u;
+        m[w] &= rows & cols;
+    }
     int cnt = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) cnt += __popc(m[w]);
@@ -616,17 +640,15 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
         if (lane >= o) incl += y;
     }
     int pos = incl - cnt;
-    // bit l of word w: lane l's bit q = (lane - l) mod 32 of its word w, the
-    // pixel of row r0 + 8w + (q >> 2), column 4l + (q & 3)
+    // pixel of bit b of word w: row r0 + 8w + (b & 7), column 4l + (b >> 3)
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         uint32_t mw = m[w];
-        const int base = (r0 + 8 * w) * G::SW;
+        const int base = (r0 + 8 * w) * G::SW + 4 * lane;
         while (mw) {
-            const int l = 31 - __clz(mw);
-            mw ^= 1u << l;
-            const int q = (lane - l) & 31;
-            const int e = base + (q >> 2) * G::SW + 4 * l + (q & 3);
+            const int b = 31 - __clz(mw);
+            mw ^= 1u << b;
+            const int e = base + (b & 7) * G::SW + (b >> 3);
             if (vio_guard(pos < G::QCAP && e < G::SR * G::SW, status)) queue[pos] = (uint16_t)e;
             ++pos;
         }
@@ -912,14 +934,20 @@ static __global__ void __launch_bounds__(256) decode_kernel(const uint8_t* __res
     const int nf = cv.h->n_frames, total = cv.h->n_cells;
     int32_t* counts = cv.h->counts;
     const int lane = threadIdx.x & 31;
+    // the cell prefix sums in shared memory when they fit (see pyramid_kernel)
+    __shared__ int32_t cells_sh[kPrefixCache];
+    const int32_t* cells = nf < kPrefixCache ? cells_sh : cv.cells;
+    if (nf < kPrefixCache)
+        for (int j = threadIdx.x; j <= nf; j += blockDim.x) cells_sh[j] = cv.cells[j];
+    __syncthreads();
     for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
         const int i = base + threadIdx.x;
         int f = -1;
         bool hit = false;
         if (i < total) {
-            f = upper_index(cv.cells, nf, i);
+            f = upper_index(cells, nf, i);
             const FrameDesc& fd = cv.fds[f];
-            const int c = i - cv.cells[f];
+            const int c = i - cells[f];
             const uint64_t key = fd.keys[c];
             int4 rec = make_int4(-1, -1, -1, 0);
             if (key != 0) {

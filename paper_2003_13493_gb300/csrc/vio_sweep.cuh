@@ -46,7 +46,7 @@ struct SweepGeom : TileGeom<TH, 1> {
 template <int PITCH>
 __device__ __forceinline__ void sweep_windows8(const uint8_t* __restrict__ p, uint32_t (&W8)[16]) {
     const uint32_t c = p[0];
-    const uint32_t K = (256u - c) | ((256u + c) << 16);
+    const uint32_t K = 256u * 0x00010001u + c * 0xFFFFu;  // (256 - c) | (256 + c) << 16, no borrow
     uint32_t D[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) D[i] = K + (uint32_t)p[circ_dy(i) * PITCH + circ_dx(i)] * 0xFFFF0001u;
@@ -311,15 +311,21 @@ static __global__ void __launch_bounds__(256) sweep_decode_kernel(const uint8_t*
     const int nf = cv.h->n_frames, cells = cv.h->n_cells;
     const int total = sw->n_set * cells;
     const int lane = threadIdx.x & 31;
+    // the cell prefix sums in shared memory when they fit (see pyramid_kernel)
+    __shared__ int32_t cells_sh[kPrefixCache];
+    const int32_t* cell_pre = nf < kPrefixCache ? cells_sh : cv.cells;
+    if (nf < kPrefixCache)
+        for (int j = threadIdx.x; j <= nf; j += blockDim.x) cells_sh[j] = cv.cells[j];
+    __syncthreads();
     for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
         const int i = base + threadIdx.x;
         int g = -1;  // (setting, frame) group of this thread
         bool hit = false;
         if (i < total) {
             const int s = i / cells, ci = i - s * cells;
-            const int f = upper_index(cv.cells, nf, ci);
+            const int f = upper_index(cell_pre, nf, ci);
             const FrameDesc& fd = cv.fds[f];
-            const int c = ci - cv.cells[f];
+            const int c = ci - cell_pre[f];
             uint64_t* kp = fd.keys + s * sw->set_stride + c;
             const uint64_t key = *kp;
             int4 rec = make_int4(-1, -1, -1, 0);

@@ -65,7 +65,8 @@ TRACK_RESULT_WORDS = 8  # x, y, gain, offset (float) | status, iters (int32) | r
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
-                ("cta_per_sm", ctypes.c_int), ("variant", ctypes.c_int), ("nms_radius", ctypes.c_int)]
+                ("cta_per_sm", ctypes.c_int), ("variant", ctypes.c_int), ("nms_radius", ctypes.c_int),
+                ("cell_size", ctypes.c_int)]
 
 
 _lib = None
@@ -160,6 +161,10 @@ def load(build_if_missing: bool = True):
     lib.vio_serve_stop.restype = st
     lib.vio_detect_noalloc.argtypes = [P, Dims, ci, ci, ci, ci, ci, P, P, P]
     lib.vio_detect_noalloc.restype = st
+    lib.vio_autotune_log.argtypes = [P, ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_float), ci]
+    lib.vio_autotune_log.restype = ci
+    lib.vio_copy_level.argtypes = [P, ci, ci, P, ci, P]
+    lib.vio_copy_level.restype = st
     lib.vio_num_variants.argtypes = []
     lib.vio_num_variants.restype = ci
     lib.vio_variant.argtypes = [ci, ctypes.POINTER(Tuning)]
@@ -286,12 +291,13 @@ class Detector:
             fptr[i] = f.data_ptr()
         dev = frames[0].device
         if outs is None:
-            outs = [torch.empty((num_cells(d.w, d.h, cell), 4), dtype=torch.int32, device=dev) for d in dims]
+            outs = [torch.empty((num_cells(d.w, d.h, cell or 32), 4), dtype=torch.int32, device=dev) for d in dims]
         if counts is None:
             counts = torch.empty(n, dtype=torch.int32, device=dev)
         optr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
         self._check(self.lib.vio_detect(self.ctx, fptr, dims, n, thresh, arc_len, cell, levels, optr,
                                         ctypes.c_void_p(counts.data_ptr()), _stream_handle(stream)))
+        self._last_dims = [(d.w, d.h) for d in dims]
         return outs, counts
 
     def track(self, prev, nxt, pts, params: dict | None = None, outs=None, stream=None):
@@ -395,6 +401,7 @@ class Detector:
         ar = (ctypes.c_int * npar)(*[p[1] for p in params])
         self._check(self.lib.vio_detect_sweep(self.ctx, fptr, dims, n, th, ar, npar, cell, levels, optr,
                                               ctypes.c_void_p(counts.data_ptr()), _stream_handle(stream)))
+        self._last_dims = [(d.w, d.h) for d in dims]
         return outs, counts
 
     def detect_sweep_ptrs(self, fptr, dims, n, th, ar, npar, cell, levels, optr, counts_ptr, stream_handle):
@@ -426,6 +433,7 @@ class Detector:
         self._check(self.lib.vio_detect_host(self.ctx, fptr, dims, n, thresh, arc_len, cell, levels, optr,
                                              ctypes.c_void_p(counts.ctypes.data),
                                              _stream_handle(stream) if stream is not None else ctypes.c_void_p(0)))
+        self._last_dims = [(d.w, d.h) for d in dims]
         return outs, counts
 
     def detect_host_batch(self, batch: "HostBatch", thresh: int, arc_len: int, cell: int, levels: int,
@@ -461,6 +469,23 @@ class Detector:
         ms = (ctypes.c_float * 3)()
         self._check(self.lib.vio_stage_ms(self.ctx, ms))
         return ms[0], ms[1], ms[2]
+
+    def copy_level(self, frame: int, level: int, stream=None) -> np.ndarray:
+        """Level `level` of frame `frame` of the most recent detection call
+        (host copy; waits for the stream)."""
+        d = self._last_dims_of(frame)
+        w, h = d[0] >> level, d[1] >> level
+        out = np.empty((h, w), dtype=np.uint8)
+        self._check(self.lib.vio_copy_level(self.ctx, frame, level, ctypes.c_void_p(out.ctypes.data), w,
+                                            _stream_handle(stream)))
+        self.sync(stream)
+        return out
+
+    def _last_dims_of(self, frame: int):
+        dims = getattr(self, "_last_dims", None)
+        if dims is None or not 0 <= frame < len(dims):
+            raise VioError(1, "no such frame in the most recent detection")
+        return dims[frame]
 
     def sync(self, stream=None):
         self._check(self.lib.vio_sync(self.ctx, _stream_handle(stream)))
@@ -516,12 +541,29 @@ class Detector:
     def serve_stop(self):
         self._check(self.lib.vio_serve_stop(self.ctx))
 
-    def set_variant(self, variant: int | None):
+    def set_variant(self, variant: int | None, cta_per_sm: int = 0):
+        """Pins a tile variant (and a CTA count per SM, 0 = as many as fit);
+        None unpins both."""
         if variant is None:
             self._check(self.lib.vio_set_tuning(self.ctx, None))
             return
-        t = Tuning(0, 0, 0, variant, 0)
+        t = Tuning(0, 0, cta_per_sm, variant, 0, 0)
         self._check(self.lib.vio_set_tuning(self.ctx, ctypes.byref(t)))
+
+    def tuning_full(self) -> dict:
+        """The launch configuration of the most recent detection."""
+        t = Tuning()
+        self._check(self.lib.vio_get_tuning(self.ctx, ctypes.byref(t)))
+        return {name: getattr(t, name) for name, _ in Tuning._fields_}
+
+    def autotune_log(self) -> list[dict]:
+        """What the most recent tuning run timed: configuration and ms per call."""
+        n = self.lib.vio_autotune_log(self.ctx, None, None, 0)
+        cfgs = (Tuning * max(1, n))()
+        ms = (ctypes.c_float * max(1, n))()
+        self.lib.vio_autotune_log(self.ctx, cfgs, ms, n)
+        return [{**{name: getattr(cfgs[i], name) for name, _ in Tuning._fields_}, "ms": round(ms[i], 5)}
+                for i in range(n)]
 
     def config(self) -> Config:
         c = Config()

@@ -521,7 +521,9 @@ def test_host_async_pipelined_on_two_streams(dets, mixed):
 def test_invalid_arguments_rejected(dets):
     img = to_gpu(synth.make_frame(64, 64, seed=1))
     d = dets[0]
-    bad = [dict(thresh=-1), dict(thresh=256), dict(arc_len=8), dict(arc_len=17), dict(cell=0),
+    # cell 0 asks the context to pick the cell size (valid); negative or
+    # non-multiples of 32 are not
+    bad = [dict(thresh=-1), dict(thresh=256), dict(arc_len=8), dict(arc_len=17), dict(cell=-32),
            dict(cell=48), dict(levels=0), dict(levels=6), dict(levels=4)]  # 64>>3 = 8 ok, 64>>4 < 7
     base = dict(thresh=10, arc_len=9, cell=32, levels=1)
     for b in bad[:-1]:
@@ -630,3 +632,80 @@ def test_wide_nms_autotune_and_tuning(mixed):
     with pytest.raises(vio.VioError):
         det.set_variant(vio.variant_ids(1)[0])
     det.close()
+
+
+def test_autotuner_picks_variant_ctas_and_cell(mixed):
+    """cell_size 0 with autotune on: the tuner times every variant x CTAs
+    per SM x cell size (32, 64) on the batch, keeps the fastest, and the
+    records equal the oracle's at the cell size it reports."""
+    imgs = mixed[::4]
+    frames = [to_gpu(im) for im in imgs]
+    det = vio.Detector(max_frames=64, autotune=True)
+    outs = [torch.full((vio.num_cells(im.shape[1], im.shape[0], 32), 4), 7, dtype=torch.int32, device="cuda")
+            for im in imgs]
+    outs, counts = det.detect(frames, 15, 9, 0, 3, outs=outs)
+    det.sync()
+    t = det.tuning_full()
+    assert t["cell_size"] in (32, 64) and 1 <= t["cta_per_sm"] <= 4 and t["variant"] in vio.variant_ids(1)
+    log = det.autotune_log()
+    combos = {(e["variant"], e["cta_per_sm"], e["cell_size"]) for e in log}
+    assert {e["cell_size"] for e in log} == {32, 64}
+    assert {e["cta_per_sm"] for e in log} >= {2, 3}
+    assert len(combos) == len(log) >= 2 * len(vio.variant_ids(1))
+    best = min(log, key=lambda e: e["ms"])
+    assert (best["variant"], best["cta_per_sm"], best["cell_size"]) == (t["variant"], t["cta_per_sm"], t["cell_size"])
+    c = t["cell_size"]
+    got = [o.cpu().numpy()[:vio.num_cells(im.shape[1], im.shape[0], c)] for o, im in zip(outs, imgs)]
+    assert_parity(got, counts.cpu().numpy(), imgs, 15, 9, c, 3, 0)
+    # a second call of the same shape reuses the choice without retuning
+    det.detect(frames, 15, 9, 0, 3, outs=outs)
+    det.sync()
+    assert det.tuning_full() == t and len(det.autotune_log()) == len(log)
+    det.close()
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 3, 4])
+def test_pinned_ctas_per_sm_identical(dets, mixed, ctas):
+    imgs = mixed[::8]
+    ref, ref_cnt = run(dets[0], imgs, 15, 9, 32, 3)
+    dets[0].set_variant(vio.variant_ids(1)[0], cta_per_sm=ctas)
+    got, cnt = run(dets[0], imgs, 15, 9, 32, 3)
+    assert dets[0].tuning_full()["cta_per_sm"] == ctas
+    dets[0].set_variant(None)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    assert np.array_equal(cnt, ref_cnt)
+    with pytest.raises(vio.VioError):
+        dets[0].set_variant(vio.variant_ids(1)[0], cta_per_sm=5)
+
+
+# ---- the pyramid levels, read back from the context ----
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_pyramid_levels_of_a_batch_match_the_oracle(dets, mixed, levels):
+    """The pyramid kernel over a large batch of mixed sizes (odd widths and
+    heights included): every pixel of every level equals the oracle's
+    pyramid, and so does the detection."""
+    imgs = mixed[::3] + [synth.make_frame(643, 479, seed=77), synth.make_frame(1283, 723, seed=78)]
+    got, cnt = run(dets[0], imgs, 15, 9, 32, levels)
+    for i, img in enumerate(imgs):
+        want = oracle.pyramid(img, levels)
+        for k in range(1, levels):
+            assert np.array_equal(dets[0].copy_level(i, k), want[k]), (i, k, img.shape)
+    assert_parity(got, cnt, imgs, 15, 9, 32, levels, 0)
+
+
+@pytest.mark.parametrize("levels", [3, 4, 5])
+def test_pyramid_levels_of_the_pyramid_kernel_match_the_oracle(dets, levels):
+    """One frame (a small call: one CTA per SM) at 3 to 5 levels, level 0
+    read back as well."""
+    img = synth.make_frame(1101, 737, seed=79)
+    frame = to_gpu(img, pitch=1120)  # kept alive: level 0 is read back from it
+    outs, counts = dets[0].detect([frame], 12, 9, 32, levels)
+    dets[0].sync()
+    want = oracle.pyramid(img, levels)
+    for k in range(levels):
+        assert np.array_equal(dets[0].copy_level(0, k), want[k]), k
+    assert_parity([outs[0].cpu().numpy()], counts.cpu().numpy(), [img], 12, 9, 32, levels, 0)
+    with pytest.raises(vio.VioError):
+        dets[0].copy_level(0, levels)

@@ -24,11 +24,14 @@ def test_byte_compare_exact():
 
 
 def test_imad_labels_exact():
-    """One multiply-add gives both Eq. 1 labels: bit 15 = brighter, bit 31 = darker."""
+    """One multiply-add gives both Eq. 1 labels: bit 15 = brighter, bit 31 = darker.
+    The per-pixel constant is itself one multiply-add of c."""
     v = np.arange(256, dtype=np.uint64)
     for t in range(256):
         for c in range(256):
             k = ((0x7FFF - c - t) & 0xFFFF) | (((0x7FFF + c - t) & 0xFFFF) << 16)
+            assert k == ((0x7FFF - t) * 0x00010001 + c * 0xFFFF) & 0xFFFFFFFF
+            assert (256 - c) | ((256 + c) << 16) == 256 * 0x00010001 + c * 0xFFFF
             w = (np.uint64(k) + v * np.uint64(0xFFFF0001)) & np.uint64(0xFFFFFFFF)
             assert np.array_equal((w >> np.uint64(15)) & np.uint64(1) == 1, np.arange(256) > c + t)
             assert np.array_equal((w >> np.uint64(31)) & np.uint64(1) == 1, np.arange(256) < c - t)
@@ -384,32 +387,35 @@ def test_sweep_window_minima_give_the_segment_test():
                 assert (best >= t + 257) == (_has_run(b, n) or _has_run(d, n)), (v, c, t, n)
 
 
-def _transpose_warp_bits(xs):
-    """transpose_warp_bits for all 32 lanes: exchange rounds with lane ^ s."""
-    M = [0x0000FFFF, 0x00FF00FF, 0x0F0F0F0F, 0x33333333, 0x55555555]
-    xs = list(xs)
-    for k in range(5):
-        sh = 16 >> k
-        ys = [xs[l ^ sh] for l in range(32)]
-        xs = [((x & ~M[k]) | ((y >> sh) & M[k])) & 0xFFFFFFFF if (l & sh) else
-              ((x & M[k]) | ((y << sh) & ~M[k])) & 0xFFFFFFFF for l, (x, y) in enumerate(zip(xs, ys))]
-    return xs
 
-
-def test_skewed_transpose_spreads_every_bit_once():
-    """Rotating lane l's word left by l and transposing gives lane b the bit
-    (b - l) mod 32 of lane l as its bit l: every candidate is walked once."""
-    rng = np.random.default_rng(14)
-    for _ in range(200):
-        words = [int(x) for x in rng.integers(0, 1 << 32, 32, dtype=np.uint64)]
-        words = [w & int(rng.integers(0, 1 << 32)) for w in words]
-        rot = [((w << l) | (w >> (32 - l))) & 0xFFFFFFFF if l else w for l, w in enumerate(words)]
-        T = _transpose_warp_bits(rot)
-        # plain transpose property
-        plain = _transpose_warp_bits(words)
-        for b in range(32):
-            for l in range(32):
-                assert (plain[b] >> l) & 1 == (words[l] >> b) & 1
-        got = sorted((l, (b - l) & 31) for b in range(32) for l in range(32) if (T[b] >> l) & 1)
-        want = sorted((l, q) for l in range(32) for q in range(32) if (words[l] >> q) & 1)
+def test_row_flag_accumulation_and_masks():
+    """coarse_and_compact's candidate words: each row's flags (bit 7 of each
+    byte) enter at the top and shift down one bit per row, so bit 8j + i of
+    word w is row 8w + i, column j; a last word of fewer than 8 rows is
+    shifted down; rows outside [row_lo, row_hi) and masked columns are
+    cleared at the end.  Decoding the set bits gives exactly the kept pixels."""
+    rng = np.random.default_rng(15)
+    for _ in range(5000):
+        rpw = int(rng.choice([4, 8, 16]))
+        r0 = rpw * int(rng.integers(0, 8))
+        lane = int(rng.integers(0, 32))
+        keeps = [int(x) for x in rng.integers(0, 1 << 32, rpw, dtype=np.uint64)]
+        vmb = int(rng.integers(0, 16))
+        vm = sum(0x80 << (8 * j) for j in range(4) if (vmb >> j) & 1)
+        row_lo, row_hi = int(rng.integers(-3, 70)), int(rng.integers(-3, 70))
+        nw = (4 * rpw + 31) // 32
+        m = [0] * nw
+        for i in range(rpw):
+            m[i // 8] = (m[i // 8] >> 1) | (keeps[i] & 0x80808080)
+        if rpw % 8:
+            m[nw - 1] >>= 8 - rpw % 8
+        cols = ((vm >> 7) & 0x01010101) * 0xFF
+        for w in range(nw):
+            lo = min(max(row_lo - r0 - 8 * w, 0), 8)
+            hi = min(max(row_hi - r0 - 8 * w, 0), 8)
+            m[w] &= ((((0xFF << lo) & ~(0xFF << hi)) & 0xFF) * 0x01010101) & cols
+        got = {(r0 + 8 * w) * 128 + 4 * lane + (b & 7) * 128 + (b >> 3)
+               for w in range(nw) for b in range(32) if (m[w] >> b) & 1}
+        want = {(r0 + i) * 128 + 4 * lane + j for i in range(rpw) for j in range(4)
+                if row_lo <= r0 + i < row_hi and (keeps[i] >> (8 * j + 7)) & 1 and (vmb >> j) & 1}
         assert got == want
