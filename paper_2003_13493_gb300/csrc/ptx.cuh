@@ -91,4 +91,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Programmatic dependent launch.  A kernel launched as a programmatic
+// dependent of the previous kernel on its stream may start while that kernel
+// is still running; griddep_wait() blocks until the previous grid has
+// completed and its memory operations are visible (a no-op for a kernel
+// launched the ordinary way), and griddep_launch_dependents() lets the next
+// kernel on the stream be scheduled before this one finishes.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace vio

@@ -211,11 +211,26 @@ vio_status enqueue_kernels(vio_ctx* ctx, int variant, int levels, cudaStream_t s
     VIO_CK_STATUS(fused_occupancy(ctx, variant, &occ));
     const int per_sm = ctas > 0 ? std::min(ctas, occ) : occ;
     const int grid = small ? ctx->sm_count : per_sm * ctx->sm_count;
-    v.fn[mode]<<<grid, kThreads, v.smem, s>>>(ctx->d_call, ctx->d_counter, ctx->d_status);
-    VIO_CK(cudaGetLastError());
+    // the detect kernel and the decode are programmatic dependents of the
+    // kernel before them: they launch while it drains and wait for it on
+    // the device (griddep_wait) before reading what it wrote
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(kThreads);
+    lc.dynamicSmemBytes = v.smem;
+    lc.stream = s;
+    lc.attrs = pdl;
+    lc.numAttrs = 1;
+    VIO_CK(cudaLaunchKernelEx(&lc, v.fn[mode], (const uint8_t*)ctx->d_call, ctx->d_counter, ctx->d_status));
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[2], s, rec_flags));
-    decode_kernel<<<small ? kSmallDecodeCtas : ctx->sm_count * 4, 256, 0, s>>>(ctx->d_call, ctx->d_counter);
-    VIO_CK(cudaGetLastError());
+    cudaLaunchConfig_t ld = lc;
+    ld.gridDim = dim3(small ? kSmallDecodeCtas : ctx->sm_count * 4);
+    ld.blockDim = dim3(256);
+    ld.dynamicSmemBytes = 0;
+    VIO_CK(cudaLaunchKernelEx(&ld, decode_kernel, (const uint8_t*)ctx->d_call, ctx->d_counter));
     if (prof) VIO_CK(cudaEventRecordWithFlags(ctx->stage_ev[3], s, rec_flags));
     return VIO_OK;
 }
@@ -463,6 +478,7 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
         f.gh = (f.h + cell - 1) / cell;
         // pyramid CTAs cover 512 columns x 8B rows of level 0
         f.pyr_bx = (f.w + 511) / 512;
+        f.pyr_magic = (uint32_t)(((1ull << 31) + f.pyr_bx - 1) / f.pyr_bx);
         const int pyr_by = (f.h + 8 * B - 1) / (8 * B);
         blocks[i + 1] = blocks[i] + (levels > 1 ? f.pyr_bx * pyr_by : 0);
         cells[i + 1] = cells[i] + f.gw * f.gh;
@@ -965,7 +981,10 @@ vio_status vio_detect_sweep(vio_ctx* ctx, const uint8_t* const* frames, const vi
             std::stable_sort(order.begin() + g0, order.begin() + std::min(n_params, g0 + kMaxSweep),
                              [&](int a, int b) { return arc_lens[a] < arc_lens[b]; });
         std::vector<int4*> outs((size_t)kMaxSweep * n);
-        const int v0 = first_variant(1);
+        // the tile table and tensor-map boxes of the sweep kernel's geometry
+        int v0 = first_variant(1);
+        for (int i = 0; i < (int)variants().size(); ++i)
+            if (variants()[i].radius == 1 && variants()[i].th == kSweepTH) v0 = i;
         for (int g0 = 0; g0 < n_params; g0 += kMaxSweep) {
             SweepSpec sp;
             sp.n_set = std::min(kMaxSweep, n_params - g0);

@@ -42,7 +42,8 @@ struct FrameDesc {
                            // memory) by the pyramid kernel, which also writes it to lev[0]
     uint8_t* lev[kMaxLevels];   // level 0 is the caller's frame (read only)
     int32_t pitch[kMaxLevels];
-    int32_t pad1[3];
+    uint32_t pyr_magic;    // ceil(2^31 / pyr_bx): block row = umulhi(2 * block, pyr_magic), exact below 2^16
+    int32_t pad1[2];
 };
 
 // Everything one call needs is uploaded as one contiguous block; this header
@@ -106,13 +107,14 @@ __device__ __forceinline__ int upper_index(const int32_t* a, int n, int v) {
 // frames (blocks[] is the per-frame prefix sum).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t pair_sums(uint32_t w) {  // [w0+w1, w2+w3] in 16-bit lanes
-    return (w & 0x00FF00FFu) + ((w >> 8) & 0x00FF00FFu);
+    return (w & 0x00FF00FFu) + __byte_perm(w, 0u, 0x4341);   // bytes 1 and 3 into the low halves
 }
 
 template <int L>
 __global__ void __launch_bounds__(256) pyramid_kernel(const uint8_t* __restrict__ call) {
     constexpr int B = 1 << (L - 1);
     constexpr int B1 = B / 2;
+    griddep_launch_dependents();
     const CallView cv(call);
     const int nf = cv.h->n_frames, nb = cv.h->n_pyr_blocks;
     // the block prefix sums, searched once per block by every thread: in
@@ -127,8 +129,9 @@ __global__ void __launch_bounds__(256) pyramid_kernel(const uint8_t* __restrict_
         const int f = upper_index(blocks, nf, b);
         const FrameDesc& fd = cv.fds[f];
         const int lb = b - blocks[f];
-        const int tx = (lb % fd.pyr_bx) * 32 + (threadIdx.x & 31);
-        const int ty = (lb / fd.pyr_bx) * 8 + (threadIdx.x >> 5);
+        const int brow = (int)__umulhi(2u * (uint32_t)lb, fd.pyr_magic);
+        const int tx = (lb - brow * fd.pyr_bx) * 32 + (threadIdx.x & 31);
+        const int ty = brow * 8 + (threadIdx.x >> 5);
         const int W = fd.w, H = fd.h;
         const int x0 = tx * 16, y0 = ty * B;
         if (x0 >= W || y0 >= H) continue;
@@ -279,61 +282,63 @@ __device__ __forceinline__ uint32_t pack4(uint32_t a, uint32_t b, uint32_t c, ui
 // 16-bit-lane minimum and maximum on the DPX unit.
 __device__ __forceinline__ uint32_t min16x2(uint32_t a, uint32_t b) { return __vimin3_u16x2(a, b, b); }
 
-// Window minima of length 8 + R over the 16 cyclic differences held two per
-// word (word j = elements 2j, 2j+1), from the windows of 8 in M8.
-template <int R>
-__device__ __forceinline__ uint32_t mt_best(const uint32_t (&M8)[8]) {
-    uint32_t W[8];
+// Window minima of the circle's signed differences (the sweep's full test,
+// the MT score).  D[i] holds point i's biased
+// differences, v - c + 256 in the low 16-bit lane (brighter) and c - v + 256
+// in the high lane (darker), both in 1..511 so no lane borrows; W8[i] is the
+// lane-wise minimum over points i .. i+7 (cyclic), from minima of three.
+__device__ __forceinline__ void window_minima8_of(const uint32_t (&v)[16], uint32_t c, uint32_t (&W8)[16]) {
+    const uint32_t K = (256u - c) | ((256u + c) << 16);
+    uint32_t D[16];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        // elements 2j + R, 2j + R + 1
-        const uint32_t S = (R & 1) ? __byte_perm(M8[(j + R / 2) & 7], M8[(j + R / 2 + 1) & 7], 0x5432)
-                                   : M8[(j + R / 2) & 7];
-        W[j] = min16x2(M8[j], S);
-    }
-    uint32_t b = __vimax3_u16x2(W[0], W[1], W[2]);
-    b = __vimax3_u16x2(b, W[3], W[4]);
-    b = __vimax3_u16x2(b, W[5], W[6]);
-    b = __vimax3_u16x2(b, W[7], W[7]);
+    for (int i = 0; i < 16; ++i) D[i] = K + v[i] * 0xFFFF0001u;
+    uint32_t W3[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) W3[i] = __vimin3_u16x2(D[i], D[(i + 1) & 15], D[(i + 2) & 15]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) W8[i] = __vimin3_u16x2(W3[i], W3[(i + 3) & 15], W3[(i + 5) & 15]);
+}
+
+// p: the candidate in a tile of row pitch PITCH bytes.
+template <int PITCH>
+__device__ __forceinline__ void window_minima8(const uint8_t* __restrict__ p, uint32_t (&W8)[16]) {
+    uint32_t v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * PITCH + circ_dx(i)];
+    window_minima8_of(v, p[0], W8);
+}
+
+// Largest minimum over the 16 windows of 8 + R points (both polarities),
+// still biased by 256: the candidate is a corner at threshold t for arc
+// length 8 + R exactly when the result is >= t + 257.  A window of 8 + R
+// points is two overlapping windows of 8, R apart.
+template <int R>
+__device__ __forceinline__ uint32_t best_window_min(const uint32_t (&W8)[16]) {
+    uint32_t m[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) m[i] = min16x2(W8[i], W8[(i + R) & 15]);
+    uint32_t b = __vimax3_u16x2(m[0], m[1], m[2]);
+    b = __vimax3_u16x2(b, m[3], m[4]);
+    b = __vimax3_u16x2(b, m[5], m[6]);
+    b = __vimax3_u16x2(b, m[7], m[8]);
+    b = __vimax3_u16x2(b, m[9], m[10]);
+    b = __vimax3_u16x2(b, m[11], m[12]);
+    b = __vimax3_u16x2(b, m[13], m[14]);
+    b = __vimax3_u16x2(b, m[15], m[15]);
     return max(b & 0xFFFFu, b >> 16);
 }
 
-// MT score (Section II-D) of a corner with circle values v, centre c and arc
-// polarity `bright`.  Raising the threshold only removes points from the
-// masks, so a window of n points that fails at the detection threshold t
-// holds a difference <= t while a passing window has all differences > t:
-// the largest minimum over all 16 windows is a passing window's and equals
-// MT + 1.  Differences (v - c for a bright arc, c - v for a dark one) are
-// biased by 256 into 16-bit lanes, two circle points per word (no borrow
-// crosses a lane: every biased value is in 1..511), and the window minima
-// are built by doubling: 2, 4, 8, then 8 + r as two overlapping windows of 8.
-__device__ __forceinline__ uint32_t mt_score(const uint32_t (&v)[16], uint32_t c, bool bright, int n) {
-    const uint32_t c2 = c * 0x00010001u;
-    uint32_t D[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const uint32_t V = __byte_perm(v[2 * j], v[2 * j + 1], 0x5410);
-        D[j] = bright ? V + (0x01000100u - c2) : (0x01000100u + c2) - V;
-    }
-    uint32_t M2[8], M4[8], M8[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) M2[j] = min16x2(D[j], __byte_perm(D[j], D[(j + 1) & 7], 0x5432));
-#pragma unroll
-    for (int j = 0; j < 8; ++j) M4[j] = min16x2(M2[j], M2[(j + 1) & 7]);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) M8[j] = min16x2(M4[j], M4[(j + 2) & 7]);
-    uint32_t best;
+__device__ __forceinline__ uint32_t best_window_min_for_arc(const uint32_t (&W8)[16], int n) {
     switch (n) {  // uniform over the launch
-        case 9: best = mt_best<1>(M8); break;
-        case 10: best = mt_best<2>(M8); break;
-        case 11: best = mt_best<3>(M8); break;
-        case 12: best = mt_best<4>(M8); break;
-        case 13: best = mt_best<5>(M8); break;
-        case 14: best = mt_best<6>(M8); break;
-        case 15: best = mt_best<7>(M8); break;
-        default: best = mt_best<8>(M8); break;
+        case 9: return best_window_min<1>(W8);
+        case 10: return best_window_min<2>(W8);
+        case 11: return best_window_min<3>(W8);
+        case 12: return best_window_min<4>(W8);
+        case 13: return best_window_min<5>(W8);
+        case 14: return best_window_min<6>(W8);
+        case 15: return best_window_min<7>(W8);
+        default: return best_window_min<8>(W8);
     }
-    return best - 257u;  // remove the bias and the final -1
 }
 
 // Full segment test and score of the pixel at shared-memory pointer p in a
@@ -358,10 +363,7 @@ __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, i
     uint32_t v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * P + circ_dx(i)];
-    // K = (0x7FFF - c - t) | (0x7FFF + c - t) << 16 as one multiply-add: the
-    // low lane never borrows (0x7FFF - t - c > 0) and the high one never
-    // carries out (0x7FFF - t + c < 2^16)
-    const uint32_t K = (0x7FFFu - (uint32_t)t) * 0x00010001u + c * 0xFFFFu;
+    const uint32_t K = ((0x7FFFu - c - (uint32_t)t) & 0xFFFFu) | ((0x7FFFu + c - (uint32_t)t) << 16);
     uint32_t w[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) w[i] = K + v[i] * 0xFFFF0001u;
@@ -399,8 +401,14 @@ __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, i
             s += __vsadu4(pack4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]) & m, c4 & m);
         }
         return s;
-    } else {  // MT: largest window minimum of the arc's polarity, minus 1
-        return mt_score(v, c, bright, n);
+    } else {  // MT: the largest t at which the pixel is still a corner
+        // = the largest minimum over all windows of n points of the signed
+        // differences, minus 1 (both polarities at once: the one that is not
+        // the corner's has no window above 0, as no pixel holds arcs of 9 of
+        // both polarities); biased by 256
+        uint32_t W8[16];
+        window_minima8_of(v, c, W8);
+        return best_window_min_for_arc(W8, n) - 257u;
     }
 }
 
@@ -781,9 +789,14 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
         for (int i = tid; i < n_tiles; i += kThreads) tiles_sh[i] = cv.tiles[i];
     __syncthreads();
 
+    griddep_launch_dependents();
     if (warp == kConsumers / 32) {
-        if (lane == 0) produce_tiles<TH, R>(cv, cached ? tiles_sh : cv.tiles, counter, status, info, full_bar, empty_bar,
-                                            smem);
+        // the pyramid levels the tiles read are written by the kernel before
+        // this one, which may still be running (programmatic dependent launch)
+        if (lane == 0) {
+            griddep_wait();
+            produce_tiles<TH, R>(cv, cached ? tiles_sh : cv.tiles, counter, status, info, full_bar, empty_bar, smem);
+        }
         return;
     }
 
@@ -930,6 +943,9 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
 // (warp-aggregated; the fused kernel zeroed the counts).
 // ---------------------------------------------------------------------------
 static __global__ void __launch_bounds__(256) decode_kernel(const uint8_t* __restrict__ call, int32_t* __restrict__ counter) {
+    // the cell keys are final once the detect kernel before this one has
+    // completed (it may still be running: programmatic dependent launch)
+    griddep_wait();
     const CallView cv(call);
     const int nf = cv.h->n_frames, total = cv.h->n_cells;
     int32_t* counts = cv.h->counts;

@@ -230,6 +230,7 @@ extern "C" vio_status vio_detect_noalloc(const uint8_t* frame, vio_dims d, int t
     fd->gw = gw;
     fd->gh = gh;
     fd->pyr_bx = (d.w + 511) / 512;
+    fd->pyr_magic = (uint32_t)(((1ull << 31) + fd->pyr_bx - 1) / fd->pyr_bx);
     fd->keys = keys;
     fd->out = reinterpret_cast<int4*>(out_cells);
     fd->lev[0] = const_cast<uint8_t*>(frame);

@@ -38,58 +38,6 @@ struct SweepGeom : TileGeom<TH, 1> {
     static constexpr int SMEM = MK_OFF + B::SR * B::SW + 128;
 };
 
-// Window minima for the sweep's full test.  D[i] holds point i's biased
-// differences, v - c + 256 in the low 16-bit lane (brighter) and c - v + 256
-// in the high lane (darker), both in 1..511 so no lane borrows; W8[i] is the
-// lane-wise minimum over points i .. i+7 (cyclic), from minima of three.
-// p: the candidate in a tile of row pitch PITCH bytes.
-template <int PITCH>
-__device__ __forceinline__ void sweep_windows8(const uint8_t* __restrict__ p, uint32_t (&W8)[16]) {
-    const uint32_t c = p[0];
-    const uint32_t K = 256u * 0x00010001u + c * 0xFFFFu;  // (256 - c) | (256 + c) << 16, no borrow
-    uint32_t D[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) D[i] = K + (uint32_t)p[circ_dy(i) * PITCH + circ_dx(i)] * 0xFFFF0001u;
-    uint32_t W3[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) W3[i] = __vimin3_u16x2(D[i], D[(i + 1) & 15], D[(i + 2) & 15]);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) W8[i] = __vimin3_u16x2(W3[i], W3[(i + 3) & 15], W3[(i + 5) & 15]);
-}
-
-// Largest minimum over the 16 windows of 8 + R points (both polarities),
-// still biased by 256: the candidate is a corner at threshold t for arc
-// length 8 + R exactly when the result is >= t + 257.  A window of 8 + R
-// points is two overlapping windows of 8, R apart.
-template <int R>
-__device__ __forceinline__ uint32_t sweep_best(const uint32_t (&W8)[16]) {
-    uint32_t m[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) m[i] = min16x2(W8[i], W8[(i + R) & 15]);
-    uint32_t b = __vimax3_u16x2(m[0], m[1], m[2]);
-    b = __vimax3_u16x2(b, m[3], m[4]);
-    b = __vimax3_u16x2(b, m[5], m[6]);
-    b = __vimax3_u16x2(b, m[7], m[8]);
-    b = __vimax3_u16x2(b, m[9], m[10]);
-    b = __vimax3_u16x2(b, m[11], m[12]);
-    b = __vimax3_u16x2(b, m[13], m[14]);
-    b = __vimax3_u16x2(b, m[15], m[15]);
-    return max(b & 0xFFFFu, b >> 16);
-}
-
-__device__ __forceinline__ uint32_t sweep_best_for_arc(const uint32_t (&W8)[16], int n) {
-    switch (n) {  // uniform over the launch
-        case 9: return sweep_best<1>(W8);
-        case 10: return sweep_best<2>(W8);
-        case 11: return sweep_best<3>(W8);
-        case 12: return sweep_best<4>(W8);
-        case 13: return sweep_best<5>(W8);
-        case 14: return sweep_best<6>(W8);
-        case 15: return sweep_best<7>(W8);
-        default: return sweep_best<8>(W8);
-    }
-}
-
 template <int TH>
 __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* __restrict__ call,
                                                                 const SweepInfo* __restrict__ sw,
@@ -158,6 +106,25 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
     const bool high_t = tmin >= 128;
     const uint32_t k7 = (uint32_t)((high_t ? 255 : 127) - tmin) * 0x01010101u;
     const int64_t stride = sw->set_stride;
+    // the usual launch has at most two arc lengths (settings ordered by arc
+    // length): then each candidate's largest window minimum is found once per
+    // arc length and the settings are 8 unrolled compares against thresholds
+    // held in registers; more arc lengths take the general loop
+    const int arc_a = set_n[0];
+    int arc_b = arc_a, n_arcs = 1;
+    for (int s = 1; s < n_set; ++s)
+        if (set_n[s] != set_n[s - 1]) {
+            ++n_arcs;
+            arc_b = set_n[s];
+        }
+    const bool two_arcs = n_arcs <= 2;
+    uint32_t thr[kMaxSweep];
+    uint32_t sel_b = 0;  // bit s: setting s has arc length arc_b
+#pragma unroll
+    for (int s = 0; s < kMaxSweep; ++s) {
+        thr[s] = s < n_set ? (uint32_t)set_t[s] + 257u : 0xFFFFFFFFu;  // >= thr: a corner in setting s
+        sel_b |= (s < n_set && set_n[s] == arc_b && arc_b != arc_a) ? 1u << s : 0u;
+    }
 
     for (int t = 0;; ++t) {
         const int b = t % NB;
@@ -210,16 +177,24 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             if (e < total && vio_guard(e < G::QCAP && queue[e] < G::SR * G::SW, status)) {
                 idx = queue[e];
                 uint32_t W8[16];
-                sweep_windows8<G::BW>(img_base + idx + 16 * (idx >> 7), W8);
-                int prev_n = 0;
-                uint32_t best = 0;
-                for (int s = 0; s < n_set; ++s) {  // uniform; settings of one arc length are adjacent
-                    const int ns = set_n[s];
-                    if (ns != prev_n) {
-                        best = sweep_best_for_arc(W8, ns);
-                        prev_n = ns;
+                window_minima8<G::BW>(img_base + idx + 16 * (idx >> 7), W8);
+                if (two_arcs) {  // uniform
+                    const uint32_t best_a = best_window_min_for_arc(W8, arc_a);
+                    const uint32_t best_b = arc_b != arc_a ? best_window_min_for_arc(W8, arc_b) : best_a;
+#pragma unroll
+                    for (int s = 0; s < kMaxSweep; ++s)
+                        cmask |= ((sel_b >> s) & 1u ? best_b : best_a) >= thr[s] ? 1u << s : 0u;
+                } else {
+                    int prev_n = 0;
+                    uint32_t best = 0;
+                    for (int s = 0; s < n_set; ++s) {  // uniform; settings of one arc length are adjacent
+                        const int ns = set_n[s];
+                        if (ns != prev_n) {
+                            best = best_window_min_for_arc(W8, ns);
+                            prev_n = ns;
+                        }
+                        if (best >= (uint32_t)set_t[s] + 257u) cmask |= 1u << s;
                     }
-                    if (best >= (uint32_t)set_t[s] + 257u) cmask |= 1u << s;
                 }
             }
             const uint32_t cm = __ballot_sync(0xFFFFFFFFu, cmask != 0);

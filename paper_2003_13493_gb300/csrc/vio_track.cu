@@ -179,6 +179,7 @@ vio_status track_impl(vio_ctx* ctx, const uint8_t* const* prev, const uint8_t* c
         fd.w = d.w;
         fd.h = d.h;
         fd.pyr_bx = (d.w + 511) / 512;
+        fd.pyr_magic = (uint32_t)(((1ull << 31) + fd.pyr_bx - 1) / fd.pyr_bx);
         const int pyr_by = (d.h + 8 * B - 1) / (8 * B);
         blocks[f + 1] = blocks[f] + (L > 1 ? fd.pyr_bx * pyr_by : 0);
         if (in_off[f] != (size_t)-1) {

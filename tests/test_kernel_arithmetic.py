@@ -24,14 +24,11 @@ def test_byte_compare_exact():
 
 
 def test_imad_labels_exact():
-    """One multiply-add gives both Eq. 1 labels: bit 15 = brighter, bit 31 = darker.
-    The per-pixel constant is itself one multiply-add of c."""
+    """One multiply-add gives both Eq. 1 labels: bit 15 = brighter, bit 31 = darker."""
     v = np.arange(256, dtype=np.uint64)
     for t in range(256):
         for c in range(256):
             k = ((0x7FFF - c - t) & 0xFFFF) | (((0x7FFF + c - t) & 0xFFFF) << 16)
-            assert k == ((0x7FFF - t) * 0x00010001 + c * 0xFFFF) & 0xFFFFFFFF
-            assert (256 - c) | ((256 + c) << 16) == 256 * 0x00010001 + c * 0xFFFF
             w = (np.uint64(k) + v * np.uint64(0xFFFF0001)) & np.uint64(0xFFFFFFFF)
             assert np.array_equal((w >> np.uint64(15)) & np.uint64(1) == 1, np.arange(256) > c + t)
             assert np.array_equal((w >> np.uint64(31)) & np.uint64(1) == 1, np.arange(256) < c - t)
@@ -128,42 +125,31 @@ def test_arc_starts_doubling():
             assert bool(r & 0xFFFF) == _has_run(m, n)
 
 
-# ---- MT score by packed window minima ----------------------------------------
+# ---- MT score by window minima of both polarities ------------------------------
 
 def _lanes(w):
     return w & 0xFFFF, w >> 16
 
 
-def _pack(lo, hi):
-    return (lo & 0xFFFF) | ((hi & 0xFFFF) << 16)
+def _min16(*ws):
+    return min(_lanes(w)[0] for w in ws) | (min(_lanes(w)[1] for w in ws) << 16)
 
 
-def _min16(a, b):
-    return _pack(min(_lanes(a)[0], _lanes(b)[0]), min(_lanes(a)[1], _lanes(b)[1]))
+def best_window_min(v, c, n):
+    """The kernel's window_minima8_of + best_window_min_for_arc: D_i =
+    (v_i - c + 256) | (c - v_i + 256) << 16, minima of three, then of eight
+    (i, i+3, i+5), a window of n = 8 + R as two windows of 8 R apart, the
+    largest over the 16 windows and both lanes."""
+    D = [(x - c + 256) | ((c - x + 256) << 16) for x in v]
+    W3 = [_min16(D[i], D[(i + 1) % 16], D[(i + 2) % 16]) for i in range(16)]
+    W8 = [_min16(W3[i], W3[(i + 3) % 16], W3[(i + 5) % 16]) for i in range(16)]
+    Wn = [_min16(W8[i], W8[(i + n - 8) % 16]) for i in range(16)]
+    return max(max(_lanes(w)) for w in Wn)
 
 
-def _perm5432(a, b):  # __byte_perm(a, b, 0x5432): high half of a, low half of b
-    return (a >> 16) | ((b & 0xFFFF) << 16)
-
-
-def mt_packed(v, c, bright, n):
-    """The kernel's MT: biased 16-bit differences two per word, window minima
-    by doubling, the largest over all 16 starts, minus the bias and 1."""
-    c2 = c * 0x00010001
-    D = []
-    for j in range(8):
-        V = v[2 * j] | (v[2 * j + 1] << 16)
-        D.append(((V + (0x01000100 - c2)) if bright else ((0x01000100 + c2) - V)) & 0xFFFFFFFF)
-    M2 = [_min16(D[j], _perm5432(D[j], D[(j + 1) & 7])) for j in range(8)]
-    M4 = [_min16(M2[j], M2[(j + 1) & 7]) for j in range(8)]
-    M8 = [_min16(M4[j], M4[(j + 2) & 7]) for j in range(8)]
-    r = n - 8
-    W = []
-    for j in range(8):
-        S = _perm5432(M8[(j + r // 2) & 7], M8[(j + r // 2 + 1) & 7]) if r & 1 else M8[(j + r // 2) & 7]
-        W.append(_min16(M8[j], S))
-    best = max(max(_lanes(w)) for w in W)
-    return best - 257
+def mt_windows(v, c, n):
+    """The MT score of a corner: largest window minimum minus the bias and 1."""
+    return best_window_min(v, c, n) - 257
 
 
 def _mt_brute(v, c, t, n):
@@ -176,7 +162,7 @@ def _mt_brute(v, c, t, n):
     return best
 
 
-def test_mt_packed_window_minima_match_brute_force():
+def test_mt_window_minima_match_brute_force():
     rng = np.random.default_rng(5)
     checked = 0
     while checked < 3000:
@@ -195,23 +181,22 @@ def test_mt_packed_window_minima_match_brute_force():
         else:
             b = sum(1 << i for i in range(16) if v[i] > c + t)
             d = sum(1 << i for i in range(16) if v[i] < c - t)
-            pol = _has_run(b, n)
-            if not (pol or _has_run(d, n)):
+            if not (_has_run(b, n) or _has_run(d, n)):
                 continue
-            assert mt_packed(v, c, pol, n) == _mt_brute(v, c, t, n), (v, c, t, n)
+            assert mt_windows(v, c, n) == _mt_brute(v, c, t, n), (v, c, t, n)
             checked += 1
 
 
-def test_mt_packed_extremes():
+def test_mt_window_minima_extremes():
     # all 16 points at the far end of the range on either side
     for c in (0, 1, 128, 254, 255):
         for n in range(9, 17):
             if c < 255:
                 v = [255] * 16
-                assert mt_packed(v, c, True, n) == 255 - c - 1 == _mt_brute(v, c, 0, n)
+                assert mt_windows(v, c, n) == 255 - c - 1 == _mt_brute(v, c, 0, n)
             if c > 0:
                 v = [0] * 16
-                assert mt_packed(v, c, False, n) == c - 1 == _mt_brute(v, c, 0, n)
+                assert mt_windows(v, c, n) == c - 1 == _mt_brute(v, c, 0, n)
 
 
 def test_nibble_to_byte_mask_exact():
@@ -419,3 +404,22 @@ def test_row_flag_accumulation_and_masks():
         want = {(r0 + i) * 128 + 4 * lane + j for i in range(rpw) for j in range(4)
                 if row_lo <= r0 + i < row_hi and (keeps[i] >> (8 * j + 7)) & 1 and (vmb >> j) & 1}
         assert got == want
+
+
+def test_pyramid_block_row_by_multiply_high():
+    """pyramid_kernel's block row: umulhi(2 * block, ceil(2^31 / pyr_bx))
+    equals block / pyr_bx for every block index below 2^16 and every
+    pyr_bx up to 256 (frames up to 131072 pixels wide; the ABI allows 65535)."""
+    for bx in range(1, 257):
+        m = ((1 << 31) + bx - 1) // bx
+        assert m < (1 << 32)
+        lb = np.arange(1 << 16, dtype=np.uint64)
+        assert np.array_equal(((2 * lb) * np.uint64(m)) >> np.uint64(32), lb // np.uint64(bx))
+
+
+def test_pair_sums_odd_bytes_by_byte_permute():
+    """pair_sums: __byte_perm(w, 0, 0x4341) moves bytes 1 and 3 into the low
+    halves of the 16-bit lanes, i.e. (w >> 8) & 0x00FF00FF."""
+    rng = np.random.default_rng(16)
+    for w in [int(x) for x in rng.integers(0, 1 << 32, 20000, dtype=np.uint64)] + [0, 0xFFFFFFFF]:
+        assert _byte_perm(w, 0, 0x4341) == (w >> 8) & 0x00FF00FF
