@@ -532,8 +532,8 @@ __device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x002
 // contiguous points contains floor(n/4) >= 2 cyclically consecutive compass
 // points (0, 4, 8, 12), all darker or all brighter and so all with
 // |I_x - I_c| > t; a pixel is kept when two adjacent compass points (n <= 11)
-// or three of the four (n >= 12) differ from the centre by more than t.  On
-// pyramid levels >= 1 (EIGHT, n <= 11) the stronger rule on the eight even
+// or three of the four (n >= 12) differ from the centre by more than t.  With
+// EIGHT (n <= 11, NMS radius <= 2) the stronger rule on the eight even
 // circle points (compass points and the (+-2, +-2) diagonals) applies: an arc
 // of n >= 9 holds floor(n/2) >= 4 cyclically consecutive even points, so a
 // pixel is kept when four consecutive of the eight differ by more than t.
@@ -834,9 +834,9 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
 #pragma unroll
             for (int j = 0; j < 4; ++j) vm |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
             const int xw = xoff / 4;
-            // levels >= 1: the 8-point test (n <= 11 and NMS radius <= 2; n >= 12 keeps 3 of 4)
+            // the 8-point test (n <= 11 and NMS radius <= 2; n >= 12 keeps 3 of 4)
             constexpr bool kEight = R <= 2;
-            if (!three && k > 0) {
+            if (!three) {
                 total = high_t ? coarse_and_compact<true, false, TH, R, kEight>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
                                : coarse_and_compact<false, false, TH, R, kEight>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
             } else if (high_t) {
