@@ -1,10 +1,12 @@
 // Fused threshold / arc-length sweep: up to 8 detector settings (threshold,
 // arc length) over the same frames in one pass.  Each tile is loaded once,
 // the coarse test runs once at the lowest threshold (its candidates are a
-// superset of every setting's), and the 16 circle values of a candidate are
-// read once.  Instead of forming Eq. 1's labels per threshold, the full test
-// finds, once per distinct arc length n, the largest threshold at which the
-// candidate is a corner: the segment test holds at t exactly when some n
+// superset of every setting's), and so does the plain segment test, at the
+// lowest threshold and the shortest arc length (its corners are a superset
+// of every setting's).  Instead of forming Eq. 1's labels per threshold, the
+// survivors' second test finds, once per distinct arc length n, the largest
+// threshold at which the candidate is a corner: the segment test holds at t
+// exactly when some n
 // cyclically consecutive signed differences (v - c for a brighter arc, c - v
 // for a darker one) all exceed t, i.e. when the largest minimum over all
 // windows of n points exceeds t.  A setting (t, n) then costs one compare.
@@ -30,6 +32,16 @@ struct SweepInfo {
     int4* const* outs;             // [n_set * n_frames] output records, setting-major
     int32_t* counts[kMaxSweep];    // per setting: [n_frames] non-empty cells, or nullptr
 };
+
+// SAD-B of circle values v around centre value c: sum of |I_x - I_c|.
+__device__ __forceinline__ uint32_t sad_b_of(const uint32_t (&v)[16], uint32_t c) {
+    const uint32_t c4 = c * 0x01010101u;
+    uint32_t s = __vsadu4(pack4(v[0], v[1], v[2], v[3]), c4);
+    s += __vsadu4(pack4(v[4], v[5], v[6], v[7]), c4);
+    s += __vsadu4(pack4(v[8], v[9], v[10], v[11]), c4);
+    s += __vsadu4(pack4(v[12], v[13], v[14], v[15]), c4);
+    return s;
+}
 
 template <int TH>
 struct SweepGeom : TileGeom<TH, 1> {
@@ -101,8 +113,11 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
     const uint32_t lt_mask = (1u << lane) - 1u;
     // the coarse test at the lowest threshold with the two-adjacent rule
     // keeps every pixel any setting can accept
-    int tmin = set_t[0];
-    for (int s = 1; s < n_set; ++s) tmin = min(tmin, set_t[s]);
+    int tmin = set_t[0], arc_min = set_n[0];
+    for (int s = 1; s < n_set; ++s) {
+        tmin = min(tmin, set_t[s]);
+        arc_min = min(arc_min, set_n[s]);
+    }
     const bool high_t = tmin >= 128;
     const uint32_t k7 = (uint32_t)((high_t ? 255 : 127) - tmin) * 0x01010101u;
     const int64_t stride = sw->set_stride;
@@ -118,12 +133,23 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             arc_b = set_n[s];
         }
     const bool two_arcs = n_arcs <= 2;
-    uint32_t thr[kMaxSweep];
-    uint32_t sel_b = 0;  // bit s: setting s has arc length arc_b
+    // settings 2j and 2j+1 in the two 16-bit lanes of tpair[j]: threshold +
+    // 257 (an unused setting gets 0x7FFF, which no window minimum reaches),
+    // and in nibble pairs of selp a byte-permute selector that takes each
+    // lane's window minimum from best_a (bytes 0-1) or best_b (bytes 2-3)
+    uint32_t tpair[kMaxSweep / 2], selp[kMaxSweep / 4] = {0u, 0u};
 #pragma unroll
-    for (int s = 0; s < kMaxSweep; ++s) {
-        thr[s] = s < n_set ? (uint32_t)set_t[s] + 257u : 0xFFFFFFFFu;  // >= thr: a corner in setting s
-        sel_b |= (s < n_set && set_n[s] == arc_b && arc_b != arc_a) ? 1u << s : 0u;
+    for (int j = 0; j < kMaxSweep / 2; ++j) {
+        uint32_t pr = 0, sl = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int s = 2 * j + h;
+            const bool use_b = s < n_set && set_n[s] == arc_b && arc_b != arc_a;
+            pr |= (s < n_set ? (uint32_t)set_t[s] + 257u : 0x7FFFu) << (16 * h);
+            sl |= (use_b ? 0x32u : 0x10u) << (8 * h);
+        }
+        tpair[j] = pr;
+        selp[j / 2] |= sl << (16 * (j & 1));
     }
 
     for (int t = 0;; ++t) {
@@ -162,28 +188,63 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
         }
         __syncwarp();
 
+        // full test, pass 1: the single-setting segment test at the lowest
+        // threshold and the shortest arc length, whose corners include every
+        // setting's (n consecutive differences beyond t >= tmin hold n_min
+        // consecutive ones beyond tmin); survivors compacted in place
+        int nsurv = 0;
+        const uint8_t* img_base = img + 3 * G::BW + xoff;
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = e0 + lane;
+            uint32_t s = 0;
+            int idx = 0;
+            if (e < total && vio_guard(e < G::QCAP && queue[e] < G::SR * G::SW, status)) {
+                idx = queue[e];
+                s = eval_corner<0, G::BW, false>(img_base + idx + 16 * (idx >> 7), tmin, arc_min);
+            }
+            const uint32_t cm = __ballot_sync(0xFFFFFFFFu, s != 0);
+            if (s) queue[nsurv + __popc(cm & lt_mask)] = (uint16_t)idx;
+            nsurv += __popc(cm);
+        }
+
         // the score and mask rows of this warp are free once its neighbours'
         // NMS of the previous tile is done
         if (!own_rows_reset<TH, 1>(nms_bar, t, sc, warp, lane, status) ||
             !own_rows_reset<TH, 1>(nms_bar, t, mk, warp, lane, status))
             return;
-        // full test of every setting; corners (in any setting) compacted in place
+        // pass 2, on the survivors: the settings in which each is a corner
+        // (window minima), its SAD-B score, compacted in place again
         int ncorner = 0;
-        const uint8_t* img_base = img + 3 * G::BW + xoff;
-        for (int e0 = 0; e0 < total; e0 += 32) {
+        for (int e0 = 0; e0 < nsurv; e0 += 32) {
             const int e = e0 + lane;
-            uint32_t cmask = 0;
+            uint32_t cmask = 0, score = 0;
             int idx = 0;
-            if (e < total && vio_guard(e < G::QCAP && queue[e] < G::SR * G::SW, status)) {
+            if (e < nsurv) {
                 idx = queue[e];
+                const uint8_t* p = img_base + idx + 16 * (idx >> 7);
+                uint32_t v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = p[circ_dy(i) * G::BW + circ_dx(i)];
+                const uint32_t c = p[0];
+                // the score first, so that the circle values die as the
+                // window minima are formed
+                score = sad_b_of(v, c);
                 uint32_t W8[16];
-                window_minima8<G::BW>(img_base + idx + 16 * (idx >> 7), W8);
+                window_minima8_of(v, c, W8);
                 if (two_arcs) {  // uniform
                     const uint32_t best_a = best_window_min_for_arc(W8, arc_a);
                     const uint32_t best_b = arc_b != arc_a ? best_window_min_for_arc(W8, arc_b) : best_a;
+                    // per pair: lane value 0x8000 + best - (t + 257) stays
+                    // in 1 .. 0x81FF (no carry or borrow between the lanes)
+                    // and has bit 15 set exactly when best >= t + 257
+                    const uint32_t bb = best_a | (best_b << 16);
+                    uint32_t z = 0;
 #pragma unroll
-                    for (int s = 0; s < kMaxSweep; ++s)
-                        cmask |= ((sel_b >> s) & 1u ? best_b : best_a) >= thr[s] ? 1u << s : 0u;
+                    for (int j = 0; j < kMaxSweep / 2; ++j) {
+                        const uint32_t x = __byte_perm(bb, 0u, selp[j / 2] >> (16 * (j & 1))) + 0x80008000u - tpair[j];
+                        z |= (x & 0x80008000u) >> (15 - 2 * j);  // bits 2j and 16 + 2j
+                    }
+                    cmask = (z | (z >> 15)) & 0xFFu;
                 } else {
                     int prev_n = 0;
                     uint32_t best = 0;
@@ -201,12 +262,9 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             if (cmask) {
                 queue[ncorner + __popc(cm & lt_mask)] = (uint16_t)idx;
                 mk[idx] = (uint8_t)cmask;
+                sc[idx] = (uint16_t)score;
             }
             ncorner += __popc(cm);
-        }
-        for (int e = lane; e < ncorner; e += 32) {
-            const int idx = queue[e];
-            sc[idx] = (uint16_t)sad_b<G::BW>(img_base + idx + 16 * (idx >> 7));
         }
         // this warp is done with the image buffer, and its scores and masks are written
         __syncwarp();

@@ -373,6 +373,40 @@ def test_sweep_window_minima_give_the_segment_test():
 
 
 
+def test_sweep_packed_setting_compares():
+    """The sweep's per-setting compares, two settings per word: lane h of
+    pair j holds setting 2j + h's threshold + 257 (0x7FFF when unused), a
+    byte permute picks each lane's window minimum from best_a (bytes 0-1) or
+    best_b (bytes 2-3), and bit 15 of 0x8000 + best - (t + 257) per lane,
+    gathered to bit s, equals best >= t + 257 for every setting s."""
+    rng = np.random.default_rng(29)
+    for trial in range(3000):
+        n_set = int(rng.integers(1, 9))
+        ts = [int(x) for x in rng.integers(0, 256, n_set)]
+        use_b = [bool(x) for x in rng.integers(0, 2, n_set)]
+        if trial < 40:
+            ts = [0 if trial % 2 else 255] * n_set
+        tpair, selp = [], [0, 0]
+        for j in range(4):
+            pr = sl = 0
+            for h in range(2):
+                s = 2 * j + h
+                pr |= ((ts[s] + 257) if s < n_set else 0x7FFF) << (16 * h)
+                sl |= (0x32 if s < n_set and use_b[s] else 0x10) << (8 * h)
+            tpair.append(pr)
+            selp[j // 2] |= sl << (16 * (j & 1))
+        for best_a, best_b in [(int(a), int(b)) for a, b in rng.integers(0, 512, (8, 2))] + [(0, 511), (511, 0), (257, 256)]:
+            bb = best_a | (best_b << 16)
+            z = 0
+            for j in range(4):
+                x = (_byte_perm(bb, 0, (selp[j // 2] >> (16 * (j & 1))) & 0xFFFF) + 0x80008000 - tpair[j]) & 0xFFFFFFFF
+                z |= (x & 0x80008000) >> (15 - 2 * j)
+            cmask = (z | (z >> 15)) & 0xFF
+            want = sum(1 << s for s in range(n_set) if (best_b if use_b[s] else best_a) >= ts[s] + 257)
+            assert cmask == want, (ts, use_b, best_a, best_b)
+
+
+
 def test_row_flag_accumulation_and_masks():
     """coarse_and_compact's candidate words: each row's flags (bit 7 of each
     byte) enter at the top and shift down one bit per row, so bit 8j + i of
