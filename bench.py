@@ -376,7 +376,8 @@ def run_ours(args, rank, world, local_rank):
                    "tile": {"w": tune[0], "h": tune[1], "variant": tune[2],
                             "rows_per_warp": tune[1] // 8 + (1 if tune[1] % 8 else 0),
                             "cta_per_sm": tune_full["cta_per_sm"],
-                            "picked_by": "autotuner" if args.variant < 0 else "--variant"},
+                            "picked_by": ("fixed: the sweep kernel's tile, CTAs per SM from its occupancy" if sweep
+                                          else "autotuner" if args.variant < 0 else "--variant")},
                    "cell_picked_by": "autotuner (32 or 64)" if auto_cell else ("--cell" if args.cell else "workload"),
                    "parallelism": f"replicas x{world}, no collective"},
         "clocks": clk,

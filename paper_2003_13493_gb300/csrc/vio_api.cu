@@ -376,6 +376,9 @@ vio_status enqueue_sweep(vio_ctx* ctx, int levels, cudaStream_t s, bool pyramid,
         VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_sweep_kernel<kSweepTH>, kThreads, smem));
         ctx->grid_sweep = std::max(1, occ) * ctx->sm_count;
     }
+    // the sweep's launch shape is fixed (its tile and the CTAs per SM its
+    // registers and shared memory allow); report it like a detect's
+    ctx->last_ctas = ctx->grid_sweep / ctx->sm_count;
     fast_sweep_kernel<kSweepTH><<<ctx->grid_sweep, kThreads, smem, s>>>(ctx->d_call, d_sw, ctx->d_counter,
                                                                       ctx->d_status);
     VIO_CK(cudaGetLastError());
