@@ -376,9 +376,6 @@ vio_status enqueue_sweep(vio_ctx* ctx, int levels, cudaStream_t s, bool pyramid,
         VIO_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_sweep_kernel<kSweepTH>, kThreads, smem));
         ctx->grid_sweep = std::max(1, occ) * ctx->sm_count;
     }
-    // the sweep's launch shape is fixed (its tile and the CTAs per SM its
-    // registers and shared memory allow); report it like a detect's
-    ctx->last_ctas = ctx->grid_sweep / ctx->sm_count;
     fast_sweep_kernel<kSweepTH><<<ctx->grid_sweep, kThreads, smem, s>>>(ctx->d_call, d_sw, ctx->d_counter,
                                                                       ctx->d_status);
     VIO_CK(cudaGetLastError());
@@ -562,7 +559,9 @@ vio_status launch(vio_ctx* ctx, int variant, const uint8_t* const* lev0, const i
     ctx->have_last = true;
     int occ = 1;
     if (!sweep) VIO_CK_STATUS(fused_occupancy(ctx, variant, &occ));
-    ctx->last_ctas = small ? 1 : (ctas > 0 ? std::min(ctas, occ) : occ);
+    // a sweep's launch shape is fixed: the CTAs per SM its registers and
+    // shared memory allow
+    ctx->last_ctas = sweep ? ctx->grid_sweep / ctx->sm_count : small ? 1 : (ctas > 0 ? std::min(ctas, occ) : occ);
     ctx->last_cell = cell;
     return VIO_OK;
 }
