@@ -407,6 +407,56 @@ def test_sweep_packed_setting_compares():
 
 
 
+def test_two_ended_walk_emits_every_bit_once():
+    """The detect kernel's compaction walk: each step takes the highest set
+    bit (31 - clz) and the lowest (the isolated bit m & -m), clears both with
+    m &= (m - 1) & ~high, and writes the second only when the two differ; the
+    written bits are the mask's bits, each once."""
+    rng = np.random.default_rng(41)
+    masks = [0, 1, 1 << 31, 0xFFFFFFFF, 0x80000001, 0x00010000] + [int(x) for x in rng.integers(0, 2**32, 3000, dtype=np.uint64)]
+    masks += [int(x) & int(y) & int(z) for x, y, z in rng.integers(0, 2**32, (2000, 3), dtype=np.uint64)]
+    for m in masks:
+        out, mw, steps = [], m, 0
+        while mw:
+            bh = mw.bit_length() - 1
+            lowbit = mw & ((-mw) & 0xFFFFFFFF)
+            bl = lowbit.bit_length() - 1
+            hb = 1 << bh
+            mw &= ((mw - 1) & 0xFFFFFFFF) & (~hb & 0xFFFFFFFF)
+            out.append(bh)
+            if lowbit != hb:
+                out.append(bl)
+            steps += 1
+        assert sorted(out) == [b for b in range(32) if (m >> b) & 1], hex(m)
+        assert steps == (bin(m).count("1") + 1) // 2
+
+
+def test_sweep_first_pass_keeps_every_setting():
+    """The sweep's first pass tests the lowest threshold and the shortest
+    arc length of the launch: a pixel that is a corner at (t, n) with
+    t >= t_min and n >= n_min is one at (t_min, n_min)."""
+    rng = np.random.default_rng(43)
+    for trial in range(3000):
+        c = int(rng.integers(0, 256))
+        v = [int(x) for x in np.clip(c + rng.integers(-70, 71, 16), 0, 255)]
+        if trial % 2:
+            s0, L, sg = int(rng.integers(0, 16)), int(rng.integers(9, 17)), 1 if rng.random() < 0.5 else -1
+            for j in range(L):
+                v[(s0 + j) % 16] = int(np.clip(c + sg * rng.integers(1, 90), 0, 255))
+
+        def corner(t, n):
+            b = sum(1 << i for i in range(16) if v[i] > c + t)
+            d = sum(1 << i for i in range(16) if v[i] < c - t)
+            return _has_run(b, n) or _has_run(d, n)
+
+        t_min, n_min = int(rng.integers(0, 60)), int(rng.integers(9, 17))
+        for t in (t_min, t_min + 1, t_min + 7, t_min + 40, 255):
+            for n in range(n_min, 17):
+                if corner(t, n):
+                    assert corner(t_min, n_min), (v, c, t, n, t_min, n_min)
+
+
+
 def test_row_flag_accumulation_and_masks():
     """coarse_and_compact's candidate words: each row's flags (bit 7 of each
     byte) enter at the top and shift down one bit per row, so bit 8j + i of
