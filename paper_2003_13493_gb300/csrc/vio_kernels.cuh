@@ -519,6 +519,13 @@ __device__ __forceinline__ Item decode_item(const CallView& cv, const int32_t* t
     return r;
 }
 
+// Score-region index of a raw walk code (w << 10 | lane << 5 | bit b) of the
+// warp whose rows start at r0: row r0 + 8w + (b & 7), column 4 lane + (b >> 3);
+// (code >> 3) & 0x7F is that column, (code >> 7) & ~7 is 8w.
+__device__ __forceinline__ int walk_code_index(uint32_t code, int r0) {
+    return (int)(((uint32_t)r0 + (code & 7u) + ((code >> 7) & ~7u)) << 7) + (int)((code >> 3) & 0x7Fu);
+}
+
 // bits 7, 15, 23, 31 -> bits 28..31: the product's other terms stay below bit 28
 __device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x00204081u) >> 28; }
 
@@ -556,8 +563,8 @@ __device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x002
 // flags, bit 7 of each byte, enter at the top and move down one bit per
 // row); one warp scan of the popcounts places each lane's run in the queue,
 // and each lane writes its pixels by walking its set bits (with TWO_ENDED,
-// from both ends at once: faster in the detect kernel, slower in the sweep,
-// both measured).  (Spreading the
+// from both ends at once and as raw codes: faster in the detect kernel,
+// slower in the sweep, both measured).  (Spreading the
 // bits over the warp first, by a skewed bit transpose, balances the walk but
 // scatters the queue, and the full test's circle reads then conflict in
 // shared memory: slower.)
@@ -657,19 +664,20 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
         const int base = (r0 + 8 * w) * G::SW + 4 * lane;
         if (TWO_ENDED) {
             // the highest and the lowest set bit per step: half the steps,
-            // and two chains that do not depend on each other
+            // and two chains that do not depend on each other.  The queue
+            // takes the raw code w << 10 | lane << 5 | bit, which the full
+            // test turns into the pixel (see walk_code_index): the walk is
+            // as slow as its busiest lane, the full test is balanced.
+            const int cbase = (w << 10) | (lane << 5);
             while (mw) {
                 const int bh = 31 - __clz(mw);
                 const uint32_t lowbit = mw & (0u - mw);
                 const int bl = 31 - __clz(lowbit);
                 const uint32_t hb = 1u << bh;
                 mw &= (mw - 1u) & ~hb;
-                const int eh = base + (bh & 7) * G::SW + (bh >> 3);
-                const int el = base + (bl & 7) * G::SW + (bl >> 3);
-                if (vio_guard(pos < G::QCAP && eh < G::SR * G::SW, status)) queue[pos] = (uint16_t)eh;
+                if (vio_guard(pos < G::QCAP, status)) queue[pos] = (uint16_t)(cbase | bh);
                 const bool two = lowbit != hb;
-                if (two && vio_guard(pos + 1 < G::QCAP && el < G::SR * G::SW, status))
-                    queue[pos + 1] = (uint16_t)el;
+                if (two && vio_guard(pos + 1 < G::QCAP, status)) queue[pos + 1] = (uint16_t)(cbase | bl);
                 pos += two ? 2 : 1;
             }
         } else {
@@ -878,7 +886,7 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             uint32_t s = 0;
             int idx = 0;
             if (e < total && vio_guard(e < G::QCAP, status)) {
-                idx = queue[e];
+                idx = walk_code_index(queue[e], 2 * G::PPW * warp);
                 // box offset of score-region pixel (idx >> 7, idx & 127); the
                 // score is taken below, on the compacted corners only
                 if (vio_guard(idx < G::SR * G::SW, status))

@@ -431,6 +431,20 @@ def test_two_ended_walk_emits_every_bit_once():
         assert steps == (bin(m).count("1") + 1) // 2
 
 
+def test_walk_code_decodes_to_the_pixel():
+    """walk_code_index: the raw code w << 10 | lane << 5 | b of the warp whose
+    rows start at r0 is score-region pixel (r0 + 8w + (b & 7)) * 128 +
+    4 lane + (b >> 3), for every warp, mask word, lane and bit."""
+    for r0 in range(0, 128, 4):
+        for w in range(4):
+            for lane in range(32):
+                for b in range(32):
+                    code = (w << 10) | (lane << 5) | b
+                    idx = ((r0 + (code & 7) + ((code >> 7) & ~7)) << 7) + ((code >> 3) & 0x7F)
+                    assert idx == (r0 + 8 * w + (b & 7)) * 128 + 4 * lane + (b >> 3)
+
+
+
 def test_sweep_first_pass_keeps_every_setting():
     """The sweep's first pass tests the lowest threshold and the shortest
     arc length of the launch: a pixel that is a corner at (t, n) with
