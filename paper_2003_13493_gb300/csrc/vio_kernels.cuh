@@ -501,6 +501,9 @@ struct ItemInfo {
     int32_t id;            // item index; >= n_items ends the consumers' loop
     int32_t level, x0, y0;
     int32_t wk, hk, gw, gh;
+    uint32_t magic;                    // cell magic of the level
+    int32_t xoff;                      // box column of score column 0
+    int32_t row_lo, row_hi, xlo, xhi;  // testable score rows, kept score columns
     uint64_t* keys;
 };
 
@@ -767,6 +770,17 @@ __device__ __forceinline__ void produce_tiles(const CallView& cv, const int32_t*
         in.gw = fd.gw;
         in.gh = fd.gh;
         in.keys = fd.keys;
+        // per-item constants, computed once here instead of by every
+        // consumer warp: score column 0 is level x = x0 - 4 and box column
+        // 0 is (x0 - 8) & ~15; score row r is level y = y0 - R + r; testable
+        // pixels are 3 <= x < Wk - 3, 3 <= y < Hk - 3; the NMS reads score
+        // columns 4 - R .. 123 + R only
+        in.magic = cv.h->cell_magic[wi.level];
+        in.xoff = in.x0 - 4 - ((in.x0 - 8) & ~15);
+        in.row_lo = max(0, 3 - in.y0 + R);
+        in.row_hi = min(G::SR, in.hk - 3 - in.y0 + R);
+        in.xlo = max(4 - R, 7 - in.x0);
+        in.xhi = min(124 + R, in.wk + 1 - in.x0);
         const CUtensorMap* map =
             wi.level == 0 ? &cv.maps0[wi.frame] : &cv.mapsk[wi.frame * (kMaxLevels - 1) + wi.level - 1];
         fence_tensormap_acquire(map);
@@ -846,22 +860,21 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
         const ItemInfo in = info[b];
         if (in.id >= n_items) break;
         const uint8_t* img = smem + G::IMG_OFF + b * G::BOXA;
-        const int k = in.level, Wk = in.wk, Hk = in.hk, x0 = in.x0, y0 = in.y0;
-        const uint32_t magic = cv.h->cell_magic[k];
-        // score column 0 is level x = x0 - 4; box column 0 is ((x0 - 8) & ~15)
-        const int xoff = x0 - 4 - ((x0 - 8) & ~15);  // 4 or 12
+        const int k = in.level, Wk = in.wk, x0 = in.x0, y0 = in.y0;
+        const uint32_t magic = in.magic;
+        const int xoff = in.xoff;
 
         // 2. coarse test + compaction.  Testable pixels: 3 <= x < Wk-3, 3 <= y < Hk-3.
         int total;
         {
             // score row r is level y = y0 - R + r; score column c is level x = x0 - 4 + c
-            const int row_lo = max(0, 3 - y0 + R), row_hi = min(G::SR, Hk - 3 - y0 + R);
-            // NMS needs scores of score columns 4-R .. 123+R (x0-R .. x0+119+R) only
-            const int sx = 4 * lane;                  // score column of this lane's first pixel
-            const int xlo = max(4 - R, 7 - x0), xhi = min(124 + R, Wk + 1 - x0);  // kept score columns [xlo, xhi)
-            uint32_t vm = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) vm |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
+            const int row_lo = in.row_lo, row_hi = in.row_hi;
+            // vm: bit 7 of byte j set when xlo <= 4 lane + j < xhi; byte j of
+            // cols4 + (128 - x) reaches bit 7 exactly when 4 lane + j >= x
+            // (all values below 256: no carries between bytes)
+            const uint32_t cols4 = (uint32_t)(4 * lane) * 0x01010101u + 0x03020100u;
+            const uint32_t vm = (cols4 + (uint32_t)(0x80 - in.xlo) * 0x01010101u) &
+                                ~(cols4 + (uint32_t)(0x80 - in.xhi) * 0x01010101u) & 0x80808080u;
             const int xw = xoff / 4;
             // the 8-point test (n <= 11 and NMS radius <= 2; n >= 12 keeps 3 of 4)
             constexpr bool kEight = R <= 2;

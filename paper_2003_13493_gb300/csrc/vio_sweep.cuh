@@ -161,18 +161,17 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
         const ItemInfo in = info[b];
         if (in.id >= n_items) break;
         const uint8_t* img = smem + G::IMG_OFF + b * G::BOXA;
-        const int k = in.level, Wk = in.wk, Hk = in.hk, x0 = in.x0, y0 = in.y0;
-        const uint32_t magic = cv.h->cell_magic[k];
-        const int xoff = x0 - 4 - ((x0 - 8) & ~15);
+        const int k = in.level, Wk = in.wk, x0 = in.x0, y0 = in.y0;
+        const uint32_t magic = in.magic;
+        const int xoff = in.xoff;
 
         int total;
         {
-            const int row_lo = max(0, 4 - y0), row_hi = min(G::SR, Hk - 2 - y0);
-            const int sx = 4 * lane;
-            const int xlo = max(3, 7 - x0), xhi = min(125, Wk + 1 - x0);
-            uint32_t vm = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) vm |= (sx + j >= xlo && sx + j < xhi) ? 0x80u << (8 * j) : 0u;
+            // the producer's per-item rows and columns (NMS radius 1)
+            const int row_lo = in.row_lo, row_hi = in.row_hi;
+            const uint32_t cols4 = (uint32_t)(4 * lane) * 0x01010101u + 0x03020100u;
+            const uint32_t vm = (cols4 + (uint32_t)(0x80 - in.xlo) * 0x01010101u) &
+                                ~(cols4 + (uint32_t)(0x80 - in.xhi) * 0x01010101u) & 0x80808080u;
             const int xw = xoff / 4;
             // levels >= 1: the 8-point test, also a necessary condition for every arc length
             if (k > 0)
