@@ -314,10 +314,12 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
                 const int leader = __ffs(any) - 1;
                 const uint32_t c = __shfl_sync(0xFFFFFFFFu, cell_id, leader);
                 const bool one_cell = __all_sync(0xFFFFFFFFu, keep == 0 || cell_id == c);
-                for (int s = 0; s < n_set; ++s) {  // uniform
+                // only the settings in which some lane keeps a corner (a
+                // ballot and a branch per empty setting cost 7 % of the kernel)
+                for (uint32_t kor = __reduce_or_sync(0xFFFFFFFFu, keep); kor; kor &= kor - 1u) {  // uniform
+                    const int s = __ffs(kor) - 1;
                     const uint32_t hs = (keep >> s) & 1u ? hi : 0u;
                     const uint32_t surv = __ballot_sync(0xFFFFFFFFu, hs != 0);
-                    if (!surv) continue;
                     unsigned long long* keys = reinterpret_cast<unsigned long long*>(in.keys + s * stride);
                     if (one_cell) {
                         const uint32_t hmax = __reduce_max_sync(0xFFFFFFFFu, hs);
