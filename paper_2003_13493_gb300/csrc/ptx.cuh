@@ -27,6 +27,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+// 64-bit unsigned maximum into global memory without a returned value (a
+// reduction the memory system performs; the thread does not wait for it).
+__device__ __forceinline__ void red_max_u64(unsigned long long* addr, unsigned long long v) {
+    asm volatile("red.global.max.u64 [%0], %1;" ::"l"(addr), "l"(v) : "memory");
+}
+
 // Plain arrival (release semantics at CTA scope): the writes this thread made
 // before it are visible to threads that observe the phase completing.
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
