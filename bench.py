@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import csv
+import gc
 import hashlib
 import io
 import json
@@ -967,6 +968,9 @@ def serving_leg(args, dev_index: int) -> dict:
                         mem_budget_bytes=4 << 30, queue_capacity=1 << 20, **kw)
         lag = 0.0
         rejected = 0
+        # no garbage-collection pause inside the paced submission loop
+        gc_was_on = gc.isenabled()
+        gc.disable()
         t0 = time.perf_counter()
         for (t, s, j) in events:
             while True:
@@ -977,6 +981,8 @@ def serving_leg(args, dev_index: int) -> dict:
             st, _ = det.submit_raw(s, pools[s][j].data_ptr(), dims[s][j])
             rejected += st != 0
         det.drain(600000)
+        if gc_was_on:
+            gc.enable()
         stats = det.serve_stats()
         det.serve_stop()
         det.close()
@@ -1065,6 +1071,8 @@ def serving_saturation_leg(args, dev_index: int) -> dict:
         det.serve_start(**cfg)
         lag = 0.0
         rejected = 0
+        gc_was_on = gc.isenabled()
+        gc.disable()
         t0 = time.perf_counter()
         for (t, s, j) in events:
             while True:
@@ -1075,6 +1083,8 @@ def serving_saturation_leg(args, dev_index: int) -> dict:
             st, _ = det.submit_raw(s, ptrs[s][j], dims[s][j])
             rejected += st != 0
         det.drain(600000)
+        if gc_was_on:
+            gc.enable()
         st = det.serve_stats()
         det.serve_stop()
         det.close()
