@@ -563,14 +563,13 @@ __device__ __forceinline__ uint32_t nibble(uint32_t keep) { return (keep * 0x002
 // word (bit 8j + i of word w = row r0 + 8w + i, column 4l + j: each row's
 // flags, bit 7 of each byte, enter at the top and move down one bit per
 // row); one warp scan of the popcounts places each lane's run in the queue,
-// and each lane writes its pixels by walking its set bits (with TWO_ENDED,
-// from both ends at once and as raw codes: faster in the detect kernel,
-// slower in the sweep, both measured).  (Spreading the
+// and each lane writes its pixels by walking its set bits, from both ends
+// at once, as raw codes.  (Spreading the
 // bits over the warp first, by a skewed bit transpose, balances the walk but
 // scatters the queue, and the full test's circle reads then conflict in
 // shared memory: slower.)
 // vm: bit 7 of byte j set when column 4l + j is inside the columns NMS reads.
-template <bool HIGH_T, bool THREE, int TH, int R, bool EIGHT = false, bool TWO_ENDED = false>
+template <bool HIGH_T, bool THREE, int TH, int R, bool EIGHT = false>
 __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* queue, int xw, uint32_t k7,
                                                   int warp, int lane, int row_lo, int row_hi, uint32_t vm,
                                                   uint32_t* status = nullptr) {
@@ -658,37 +657,26 @@ __device__ __forceinline__ int coarse_and_compact(const uint8_t* img, uint16_t* 
         if (lane >= o) incl += y;
     }
     int pos = incl - cnt;
-    // pixel of bit b of word w: row r0 + 8w + (b & 7), column 4l + (b >> 3)
+    // bit b of word w stands for row r0 + 8w + (b & 7), column 4l + (b >> 3)
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         uint32_t mw = m[w];
-        const int base = (r0 + 8 * w) * G::SW + 4 * lane;
-        if (TWO_ENDED) {
-            // the highest and the lowest set bit per step: half the steps,
-            // and two chains that do not depend on each other.  The queue
-            // takes the raw code w << 10 | lane << 5 | bit, which the full
-            // test turns into the pixel (see walk_code_index): the walk is
-            // as slow as its busiest lane, the full test is balanced.
-            const int cbase = (w << 10) | (lane << 5);
-            while (mw) {
-                const int bh = 31 - __clz(mw);
-                const uint32_t lowbit = mw & (0u - mw);
-                const int bl = 31 - __clz(lowbit);
-                const uint32_t hb = 1u << bh;
-                mw &= (mw - 1u) & ~hb;
-                if (vio_guard(pos < G::QCAP, status)) queue[pos] = (uint16_t)(cbase | bh);
-                const bool two = lowbit != hb;
-                if (two && vio_guard(pos + 1 < G::QCAP, status)) queue[pos + 1] = (uint16_t)(cbase | bl);
-                pos += two ? 2 : 1;
-            }
-        } else {
-            while (mw) {
-                const int b = 31 - __clz(mw);
-                mw ^= 1u << b;
-                const int e = base + (b & 7) * G::SW + (b >> 3);
-                if (vio_guard(pos < G::QCAP && e < G::SR * G::SW, status)) queue[pos] = (uint16_t)e;
-                ++pos;
-            }
+        // the highest and the lowest set bit per step: half the steps, and
+        // two chains that do not depend on each other.  The queue takes the
+        // raw code w << 10 | lane << 5 | bit, which the full test turns into
+        // the pixel (walk_code_index): the walk is as slow as its busiest
+        // lane, the full test is balanced.
+        const int cbase = (w << 10) | (lane << 5);
+        while (mw) {
+            const int bh = 31 - __clz(mw);
+            const uint32_t lowbit = mw & (0u - mw);
+            const int bl = 31 - __clz(lowbit);
+            const uint32_t hb = 1u << bh;
+            mw &= (mw - 1u) & ~hb;
+            if (vio_guard(pos < G::QCAP, status)) queue[pos] = (uint16_t)(cbase | bh);
+            const bool two = lowbit != hb;
+            if (two && vio_guard(pos + 1 < G::QCAP, status)) queue[pos + 1] = (uint16_t)(cbase | bl);
+            pos += two ? 2 : 1;
         }
     }
     return __shfl_sync(kFull, incl, 31);
@@ -877,14 +865,14 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             // the 8-point test (n <= 11 and NMS radius <= 2; n >= 12 keeps 3 of 4)
             constexpr bool kEight = R <= 2;
             if (!three) {
-                total = high_t ? coarse_and_compact<true, false, TH, R, kEight, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
-                               : coarse_and_compact<false, false, TH, R, kEight, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
+                total = high_t ? coarse_and_compact<true, false, TH, R, kEight>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
+                               : coarse_and_compact<false, false, TH, R, kEight>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
             } else if (high_t) {
-                total = three ? coarse_and_compact<true, true, TH, R, false, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
-                              : coarse_and_compact<true, false, TH, R, false, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
+                total = three ? coarse_and_compact<true, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
+                              : coarse_and_compact<true, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
             } else {
-                total = three ? coarse_and_compact<false, true, TH, R, false, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
-                              : coarse_and_compact<false, false, TH, R, false, true>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
+                total = three ? coarse_and_compact<false, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
+                              : coarse_and_compact<false, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
             }
         }
         __syncwarp();

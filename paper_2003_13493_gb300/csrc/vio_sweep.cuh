@@ -197,9 +197,10 @@ __global__ void __launch_bounds__(kThreads, 3) fast_sweep_kernel(const uint8_t* 
             const int e = e0 + lane;
             uint32_t s = 0;
             int idx = 0;
-            if (e < total && vio_guard(e < G::QCAP && queue[e] < G::SR * G::SW, status)) {
-                idx = queue[e];
-                s = eval_corner<0, G::BW, false>(img_base + idx + 16 * (idx >> 7), tmin, arc_min);
+            if (e < total && vio_guard(e < G::QCAP, status)) {
+                idx = walk_code_index(queue[e], 2 * G::PPW * warp);
+                if (vio_guard(idx < G::SR * G::SW, status))
+                    s = eval_corner<0, G::BW, false>(img_base + idx + 16 * (idx >> 7), tmin, arc_min);
             }
             const uint32_t cm = __ballot_sync(0xFFFFFFFFu, s != 0);
             if (s) queue[nsurv + __popc(cm & lt_mask)] = (uint16_t)idx;
