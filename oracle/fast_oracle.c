@@ -11,7 +11,7 @@
  * Frontend for High-Speed VIO", Nagy, Foehn, Scaramuzza, IROS 2020):
  *
  *   pyramid          Section II-B (subsampled pyramid), Section III-C
- *                    (each layer halves the previous one); 2x2 mean,
+ *                    (every level half the size of the one above); 2x2 mean,
  *                    rounded half up: (a+b+c+d+2)>>2.
  *   circle / labels  Section II-D, Eq. 1 (radius-3 Bresenham circle of 16
  *                    points; darker / similar / brighter with strict
@@ -19,7 +19,7 @@
  *   segment test     Section II-D: a contiguous arc of at least N points,
  *                    all darker or all brighter; a 3-pixel border skipped.
  *   scores           Section II-D: SAD-B, SAD-A, MT; 0 when the test fails.
- *   NMS              Algorithm 1, "per scale"; Section I-B (Moore
+ *   NMS              Algorithm 1 (on every scale); Section I-B (Moore
  *                    neighbourhood of side 2n+1: n = 1 gives 3x3, n = 2..4
  *                    the 5x5..9x9 windows of Table III).
  *   NMS-C            Algorithm 1 (after all scales), Section II-B (one
