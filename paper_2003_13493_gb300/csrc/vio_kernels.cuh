@@ -867,12 +867,9 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
             if (!three) {
                 total = high_t ? coarse_and_compact<true, false, TH, R, kEight>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
                                : coarse_and_compact<false, false, TH, R, kEight>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
-            } else if (high_t) {
-                total = three ? coarse_and_compact<true, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
-                              : coarse_and_compact<true, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
             } else {
-                total = three ? coarse_and_compact<false, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
-                              : coarse_and_compact<false, false, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
+                total = high_t ? coarse_and_compact<true, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status)
+                               : coarse_and_compact<false, true, TH, R>(img, queue, xw, k7, warp, lane, row_lo, row_hi, vm, status);
             }
         }
         __syncwarp();
