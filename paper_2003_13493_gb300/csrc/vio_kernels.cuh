@@ -907,17 +907,50 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
         // the neighbours' scores of this tile are written
         if (!neighbours_wait(sc_bar, warp, G::WARPS, t & 1, lane, status)) return;
 
-        // 4. NMS on the corners, cell maximum by a 64-bit max reduction per survivor
-        for (int e0 = 0; e0 < ncorner; e0 += 32) {
+        // 4. NMS on the corners, cell maximum by a 64-bit max reduction per
+        // survivor.  A window wider than 3x3 takes two passes: the 8 nearest
+        // neighbours of every corner first, which suppress most corners, then
+        // the outer rings for the corners that pass them (compacted to the
+        // front of the queue) only.
+        int nnms = ncorner;
+        if constexpr (R > 1) {
+            int npass = 0;
+            for (int e0 = 0; e0 < ncorner; e0 += 32) {
+                const int e = e0 + lane;
+                int idx = 0;
+                bool ok = false;
+                if (e < ncorner) {
+                    idx = queue[e];
+                    const int sr = idx >> 7, scx = idx & 127;
+                    if (scx >= 4 && scx < 4 + G::TW && sr >= R && sr < R + TH) {
+                        const uint16_t* q = sc + idx;
+                        const uint32_t s = q[0];
+                        ok = true;
+#pragma unroll
+                        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                            for (int dx = -1; dx <= 1; ++dx)
+                                if (dy != 0 || dx != 0) ok &= s >= q[dy * G::SW + dx];
+                    }
+                }
+                const uint32_t bm = __ballot_sync(0xFFFFFFFFu, ok);
+                if (ok) queue[npass + __popc(bm & lt_mask)] = (uint16_t)idx;
+                npass += __popc(bm);
+            }
+            nnms = npass;
+        }
+        for (int e0 = 0; e0 < nnms; e0 += 32) {
             const int e = e0 + lane;
             uint32_t cell_id = 0xFFFFFFFFu;
             uint32_t hi = 0, lo = 0;
-            if (e < ncorner) {
+            if (e < nnms) {
                 const int idx = queue[e];
                 const int sr = idx >> 7, scx = idx & 127;
-                const bool inside = scx >= 4 && scx < 4 + G::TW && sr >= R && sr < R + TH;
+                // (with R > 1 the first pass kept corners inside the tile only)
+                const bool inside = R > 1 || (scx >= 4 && scx < 4 + G::TW && sr >= R && sr < R + TH);
                 if (inside) {
                     // (2R+1) x (2R+1) neighbourhood: keep when >= every neighbour
+                    // (for R > 1, every neighbour beyond the 8 nearest)
                     const uint16_t* q = sc + idx;
                     const uint32_t s = q[0];
                     bool keep = true;
@@ -927,7 +960,8 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
                     for (int dy = -R; dy <= R; ++dy)
 #pragma unroll
                         for (int dx = -R; dx <= R; ++dx)
-                            if (dy != 0 || dx != 0) keep &= s >= q[dy * G::SW + dx];
+                            if ((dy != 0 || dx != 0) && (R == 1 || dy < -1 || dy > 1 || dx < -1 || dx > 1))
+                                keep &= s >= q[dy * G::SW + dx];
                     if (keep) {
                         const uint32_t x = (uint32_t)(x0 - 4 + scx), y = (uint32_t)(y0 - R + sr);
                         const uint32_t cx = __umulhi(x, magic), cy = __umulhi(y, magic);
