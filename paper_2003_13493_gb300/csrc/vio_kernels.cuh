@@ -443,23 +443,27 @@ __device__ __forceinline__ uint32_t gt_flags(uint32_t a, uint32_t b, uint32_t k7
 // Fused detect: persistent CTAs pull (frame, level, tile) items from a
 // counter.  A tile is 120 x TH level pixels; its "score region" adds a ring
 // (4 px left and right, R rows up and down for an NMS radius R) so that it is
-// exactly 128 pixels wide: 16 lanes of 8 pixels cover a row, a warp covers a
-// pair of rows.
+// exactly 128 pixels wide: lane l owns the 4-pixel word of columns 4l..4l+3
+// of every row, and each of the 8 consumer warps owns a band of consecutive
+// rows.
 // Per item:
-//   1. TMA loads the region plus the 3-pixel circle halo (box 144 x TH+2R+6)
-//      into one of two image buffers; the other buffer is loading the next
-//      item meanwhile.
-//   2. Coarse test on every score-region pixel, 8 pixels per lane (the
-//      compass rule on level 0, the 8-point rule above it), pixels outside
-//      the testable area masked off; each warp appends the kept pixels of
-//      each of its row pairs to its own queue (warp scan).
+//   1. The producer (one thread) claims the item, computes its constants
+//      and TMA loads the region plus the 3-pixel circle halo (box 144 x
+//      TH+2R+6) into one of two image buffers; the other buffer is loading
+//      the next item meanwhile.
+//   2. Coarse test on every score-region pixel of the warp's band, 4 pixels
+//      per lane (the 8-point rule for arcs n <= 11 and R <= 2, else the
+//      compass rule), pixels outside the testable area masked off; one warp
+//      scan places each lane's kept pixels in the warp's queue, written by a
+//      two-ended bit walk as raw codes (coarse_and_compact).
 //   3. Each warp runs the full segment test on its queue and compacts the
 //      corners in place, then scores the corners and writes the scores into
 //      the score tile.
 //   4. Once its two neighbouring warps have written their scores (the NMS
 //      reads up to R rows of theirs; per-warp mbarriers, see neighbours_wait),
-//      (2R+1)x(2R+1) NMS on the corner lists; each survivor folds its packed
-//      key into the global cell key with a 64-bit max reduction.
+//      (2R+1)x(2R+1) NMS on the corner list (for R > 1 the nearest ring
+//      first, the outer rings on its survivors); each survivor folds its
+//      packed key into the global cell key with a 64-bit max reduction.
 // ---------------------------------------------------------------------------
 constexpr int kTileW = 120;  // output pixels per tile row, every variant
 
