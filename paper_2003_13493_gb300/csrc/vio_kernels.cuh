@@ -412,6 +412,16 @@ __device__ __forceinline__ uint32_t eval_corner(const uint8_t* __restrict__ p, i
     }
 }
 
+// MT score of a pixel already known to be a corner for arc length n: the
+// largest minimum over the windows of n signed differences, minus 1 (biased
+// by 256 as in eval_corner).
+template <int P>
+__device__ __forceinline__ uint32_t mt_of_corner(const uint8_t* __restrict__ p, int n) {
+    uint32_t W8[16];
+    window_minima8<P>(p, W8);
+    return best_window_min_for_arc(W8, n) - 257u;
+}
+
 // SAD-B of the pixel at p (row pitch P): sum of |I_x - I_c| over the circle.
 template <int P>
 __device__ __forceinline__ uint32_t sad_b(const uint8_t* __restrict__ p) {
@@ -900,7 +910,11 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
         for (int e = lane; e < ncorner; e += 32) {
             const int idx = queue[e];
             const uint8_t* p = img_base + idx + 16 * (idx >> 7);
-            sc[idx] = (uint16_t)(MODE == 0 ? sad_b<G::BW>(p) : eval_corner<MODE, G::BW, true>(p, thresh, n_arc));
+            // MT of a known corner needs no segment test: the largest window
+            // minimum alone (see eval_corner)
+            sc[idx] = (uint16_t)(MODE == 0   ? sad_b<G::BW>(p)
+                                 : MODE == 2 ? mt_of_corner<G::BW>(p, n_arc)
+                                             : eval_corner<MODE, G::BW, true>(p, thresh, n_arc));
         }
         // this warp is done with the image buffer, and its scores are written
         __syncwarp();
