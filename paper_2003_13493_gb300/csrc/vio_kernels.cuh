@@ -789,6 +789,38 @@ __device__ __forceinline__ void produce_tiles(const CallView& cv, const int32_t*
     }
 }
 
+// NMS ring K around the score at q (row pitch SW): true when s is >= the
+// 8K scores at Chebyshev distance K.
+template <int K, int SW>
+__device__ __forceinline__ bool ring_max(const uint16_t* q, uint32_t s) {
+    bool ok = true;
+#pragma unroll
+    for (int dx = -K; dx <= K; ++dx) ok &= (s >= q[-K * SW + dx]) & (s >= q[K * SW + dx]);
+#pragma unroll
+    for (int dy = -K + 1; dy <= K - 1; ++dy) ok &= (s >= q[dy * SW - K]) & (s >= q[dy * SW + K]);
+    return ok;
+}
+
+// One NMS pass of a wide window: keeps the corners of queue[0, n) that pass
+// ring K, compacted in place; returns how many.
+template <int K, int SW>
+__device__ __forceinline__ int nms_ring_pass(uint16_t* queue, int n, const uint16_t* sc, int lane, uint32_t lt_mask) {
+    int np = 0;
+    for (int e0 = 0; e0 < n; e0 += 32) {
+        const int e = e0 + lane;
+        int idx = 0;
+        bool ok = false;
+        if (e < n) {
+            idx = queue[e];
+            ok = ring_max<K, SW>(sc + idx, sc[idx]);
+        }
+        const uint32_t bm = __ballot_sync(0xFFFFFFFFu, ok);
+        if (ok) queue[np + __popc(bm & lt_mask)] = (uint16_t)idx;
+        np += __popc(bm);
+    }
+    return np;
+}
+
 template <int TH, int MODE, int R = 1>
 __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_t* __restrict__ call,
                                                                  int32_t* __restrict__ counter,
@@ -926,10 +958,10 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
         if (!neighbours_wait(sc_bar, warp, G::WARPS, t & 1, lane, status)) return;
 
         // 4. NMS on the corners, cell maximum by a 64-bit max reduction per
-        // survivor.  A window wider than 3x3 takes two passes: the 8 nearest
-        // neighbours of every corner first, which suppress most corners, then
-        // the outer rings for the corners that pass them (compacted to the
-        // front of the queue) only.
+        // survivor.  A window wider than 3x3 is tested ring by ring: the 8
+        // nearest neighbours of every corner first, which suppress most
+        // corners, then each further ring on the corners that passed the
+        // rings inside it (compacted to the front of the queue).
         int nnms = ncorner;
         if constexpr (R > 1) {
             int npass = 0;
@@ -956,6 +988,8 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
                 npass += __popc(bm);
             }
             nnms = npass;
+            if constexpr (R > 2) nnms = nms_ring_pass<2, G::SW>(queue, nnms, sc, lane, lt_mask);
+            if constexpr (R > 3) nnms = nms_ring_pass<3, G::SW>(queue, nnms, sc, lane, lt_mask);
         }
         for (int e0 = 0; e0 < nnms; e0 += 32) {
             const int e = e0 + lane;
@@ -968,18 +1002,15 @@ __global__ void __launch_bounds__(kThreads, 4) fast_nms_cell_kernel(const uint8_
                 const bool inside = R > 1 || (scx >= 4 && scx < 4 + G::TW && sr >= R && sr < R + TH);
                 if (inside) {
                     // (2R+1) x (2R+1) neighbourhood: keep when >= every neighbour
-                    // (for R > 1, every neighbour beyond the 8 nearest)
+                    // (for R > 1 the outermost ring; the passes above did the rest)
                     const uint16_t* q = sc + idx;
                     const uint32_t s = q[0];
-                    bool keep = true;
-                    // rows one at a time beyond 3x3: a whole 9x9 window of loads in
-                    // flight would spill under the 4-CTA register budget
-#pragma unroll(R == 1 ? 3 : 1)
-                    for (int dy = -R; dy <= R; ++dy)
-#pragma unroll
-                        for (int dx = -R; dx <= R; ++dx)
-                            if ((dy != 0 || dx != 0) && (R == 1 || dy < -1 || dy > 1 || dx < -1 || dx > 1))
-                                keep &= s >= q[dy * G::SW + dx];
+                    bool keep;
+                    if constexpr (R == 1) {
+                        keep = ring_max<1, G::SW>(q, s);
+                    } else {
+                        keep = ring_max<R, G::SW>(q, s);
+                    }
                     if (keep) {
                         const uint32_t x = (uint32_t)(x0 - 4 + scx), y = (uint32_t)(y0 - R + sr);
                         const uint32_t cx = __umulhi(x, magic), cy = __umulhi(y, magic);
