@@ -445,6 +445,39 @@ def test_walk_code_decodes_to_the_pixel():
 
 
 
+def _ring_offsets(k):
+    """The offsets ring_max<K> reads: rows -K and K in full, then columns -K
+    and K of the rows between."""
+    out = []
+    for dx in range(-k, k + 1):
+        out += [(-k, dx), (k, dx)]
+    for dy in range(-k + 1, k):
+        out += [(dy, -k), (dy, k)]
+    return out
+
+
+def test_nms_rings_partition_the_window():
+    """The wide NMS windows are tested ring by ring (ring 1 on every corner,
+    ring k on the survivors of rings 1..k-1): the rings 1..R visit every
+    offset of the (2R+1)^2 window except the centre exactly once, so keeping
+    a corner that passes every ring is the plain window test."""
+    for r in range(1, 5):
+        seen = [o for k in range(1, r + 1) for o in _ring_offsets(k)]
+        assert len(seen) == len(set(seen)) == (2 * r + 1) ** 2 - 1
+        assert set(seen) == {(dy, dx) for dy in range(-r, r + 1) for dx in range(-r, r + 1)} - {(0, 0)}
+        for k in range(1, r + 1):
+            assert all(max(abs(dy), abs(dx)) == k for dy, dx in _ring_offsets(k))
+    rng = np.random.default_rng(47)
+    for _ in range(200):
+        r = int(rng.integers(2, 5))
+        tile = rng.integers(0, 6, (2 * r + 1, 2 * r + 1))
+        s = tile[r, r]
+        window = all(s >= tile[r + dy, r + dx] for dy in range(-r, r + 1) for dx in range(-r, r + 1))
+        rings = all(all(s >= tile[r + dy, r + dx] for dy, dx in _ring_offsets(k)) for k in range(1, r + 1))
+        assert window == rings
+
+
+
 def test_sweep_first_pass_keeps_every_setting():
     """The sweep's first pass tests the lowest threshold and the shortest
     arc length of the launch: a pixel that is a corner at (t, n) with
